@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the guided-filter deconvolution hot path on GB300.
+
+Workload: the uneven batch of 256 synthetic images (canvases 256^2, 512^2 and
+1024^2 from true sizes 256^2, 384^2, 512^2, 1024x768), each with its own PSF,
+noise level and window, 15 iterations.  One step = one whole batched solve
+(setup + 15 iterations of Steps 1-3) replayed from its CUDA graph, inputs
+resident in HBM.  The metric is true-pixel iterations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own batch of 256 images (weak scaling, no
+data-path collective); rank 0 prints one JSON line.  --impl reference times
+the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel-iters/s on 1 GB300, batched vs plain at ≤2e-5 vs FP64; % HBM peak"
+UNIT = "Mpixel-iter/s"
+N_IMAGES = 256
+ITERS = 15
+WORKLOAD = "batched_256_uneven_{256,384->512,512,1024x768->1024}_15it"
+# algorithmic HBM bytes per canvas pixel moved by one launch of each phase
+# (inputs read once, outputs written once; FP32 planes, packed spectra)
+PHASE_BYTES = {"row_fwd": 8, "col_fwd_lambda": 16, "lambda_pass": 12, "col_solve_inv": 20,
+               "row_inv": 16, "guided_filter": 12, "guided_filter_isnr": 16}
+B_ALG = 68  # bytes per pixel-iteration of the whole iteration (one-pass transforms)
+
+
+# ---------------------------------------------------------------------------
+# host logic shared by every rank (also exercised by the CPU tests)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_indices(rank: int, world: int, n_per_rank: int = N_IMAGES):
+    """Weak scaling: rank r owns images r*n .. r*n + n - 1 of the seeded
+    sequence (seed 1000 + index)."""
+    return list(range(rank * n_per_rank, (rank + 1) * n_per_rank))
+
+
+def reduce_max(value: float, dist=None, device=None):
+    """Max over ranks (a barrier is implied)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, dist=None, device=None):
+    if dist is None or not dist.is_initialized():
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _gen(i):
+    import synthetic
+    return synthetic.config_c2_image(i, iters=ITERS)
+
+
+def generate(indices, workers=None):
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1 or len(indices) < 4:
+        return [_gen(i) for i in indices]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_gen, indices, chunksize=4)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        load = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(probs, budget_s=None):
+    """Time the FP64 oracle, as it stands, over whole problems (all
+    iterations); returns (Mpx-iter/s, seconds, true px-iters, results)."""
+    import oracle
+    t0 = time.perf_counter()
+    work = 0
+    res = []
+    for p in probs:
+        r = oracle.solve(p.y, p.h, p.sigma, p.w, p.eps, p.iters, u_orig=p.u_orig)
+        res.append(r)
+        work += p.true_shape[0] * p.true_shape[1] * p.iters
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return work / dt / 1e6, dt, work, res
+
+
+def class_sample(probs):
+    """One image of each canvas/true-size class, in batch order."""
+    seen, out = set(), []
+    for p in probs:
+        key = (p.shape, p.true_shape)
+        if key not in seen:
+            seen.add(key)
+            out.append(p)
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    probs = class_sample(generate(list(range(64)), workers=4))
+    cores = 1
+    # each step: one whole problem of the sample (cycled), all iterations
+    for k in range(args.warmup):
+        oracle_sample([probs[k % len(probs)]])
+    t0 = time.perf_counter()
+    work = 0
+    for k in range(args.steps):
+        _, _, w, _ = oracle_sample([probs[k % len(probs)]])
+        work += w
+    dt = time.perf_counter() - t0
+    value = work / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images": N_IMAGES, "iters": ITERS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one whole image per step, cycling one image of each "
+                                   f"size class ({len(probs)} classes), {ITERS} iterations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = generate(shard_indices(rank, world))  # before any CUDA work
+    import paper_1609_01839_gb300 as gfd
+
+    true_px = sum(p.true_shape[0] * p.true_shape[1] for p in probs)
+    canvas_px = sum(p.shape[0] * p.shape[1] for p in probs)
+    items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
+              "sigma": p.sigma, "w": p.w, "eps": p.eps,
+              "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
+    ctx = gfd.Context(local)
+    arr = ctx.make_images(items, ITERS)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):  # the first call also builds and captures the graph
+        ctx.solve_batched_images(arr, ITERS, stream)
+    torch.cuda.synchronize(dev)
+    launches_per_step = ctx.last_launch_count()
+    st = ctx.status(len(items))
+
+    # timed region: K graph replays, barrier + sync on both sides
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.solve_batched_images(arr, ITERS, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = reduce_max(ms, dist, dev)
+    total_true = reduce_sum(float(true_px), dist, dev)
+    total_canvas = reduce_sum(float(canvas_px), dist, dev)
+    value = total_true * ITERS * args.steps / (ms_max / 1e3) / 1e6
+    value_canvas = total_canvas * ITERS * args.steps / (ms_max / 1e3) / 1e6
+
+    # per-phase device time (direct launches, event pair around every launch)
+    phase_ms, phase_n = ctx.solve_batched_timed(arr, ITERS, stream)
+    phases = dict(zip(gfd.PHASES, phase_ms))
+    nlaunch = dict(zip(gfd.PHASES, phase_n))
+    iter_phases = [k for k in gfd.PHASES if k not in ("setup", "copy")]
+    dom = max(iter_phases, key=lambda k: phases[k])
+    per_px = PHASE_BYTES["guided_filter_isnr" if dom == "guided_filter" else dom]
+    dom_bytes = per_px * canvas_px * ITERS  # over all launches of the phase in one solve
+    hbm_peak, peak_kind = load_peaks()
+    achieved = dom_bytes / (phases[dom] / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dom)
+        except Exception:
+            traffic = None
+
+    # plain path: the same images one gfdeconv_solve at a time (direct launches)
+    plain_n = min(args.plain_images, len(probs))
+    pctx = gfd.Context(local, use_graphs=False)
+    for it in items[:2]:
+        pctx.solve(it["y"], it["h"], it["sigma"], it["w"], it["eps"], ITERS)
+    torch.cuda.synchronize(dev)
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for it in items[:plain_n]:
+        pctx.solve(it["y"], it["h"], it["sigma"], it["w"], it["eps"], ITERS)
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = pe0.elapsed_time(pe1)
+    plain_px = sum(p.true_shape[0] * p.true_shape[1] for p in probs[:plain_n])
+    plain_value = plain_px * ITERS / (plain_ms / 1e3) / 1e6
+    pctx.close()
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hitems = [{"y": torch.from_numpy(p.y).pin_memory(), "h": torch.from_numpy(p.h).pin_memory(),
+               "sigma": p.sigma, "w": p.w, "eps": p.eps,
+               "u_orig": torch.from_numpy(p.u_orig).pin_memory()} for p in probs]
+    harr = ctx.make_host_images(hitems, ITERS)
+    h2d = sum(p.y.nbytes + p.h.nbytes + p.u_orig.nbytes for p in probs)
+    d2h = sum(p.y.nbytes + 2 * 8 * ITERS for p in probs)
+    for _ in range(2):
+        ctx.solve_batched_host_images(harr, ITERS, stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.solve_batched_host_images(harr, ITERS, stream)
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e_value = total_true * ITERS * e2e_steps / e2e_s / 1e6
+
+    # parity spot check + CPU baseline: one image of each size class, oracle FP64
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = class_sample(probs)
+        idx = [probs.index(p) for p in sample]
+        rate, secs, work, res = oracle_sample(sample)
+        errs = [float(np.abs(items[i]["u"].cpu().numpy() - r["u"]).max()) for i, r in zip(idx, res)]
+        isnr_err = [float(np.abs(items[i]["isnr"].cpu().numpy() - np.array(r["isnr"])).max())
+                    for i, r in zip(idx, res)]
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(sample)} whole images of the batch (one per size class, "
+                         f"{ITERS} iterations, {work} true px-iters) in {secs:.1f} s"}
+        parity = {"images": idx, "max_abs_u": max(errs), "max_abs_isnr_db": max(isnr_err)}
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images_per_gpu": len(probs), "iters": ITERS,
+                   "true_px_per_gpu": true_px, "canvas_px_per_gpu": canvas_px,
+                   "value_canvas_px": value_canvas,
+                   "l2": f"inputs larger than L2: {(canvas_px * 28) / 1e9:.2f} GB resident per solve",
+                   "parallelism": f"images sharded over {world} GPU(s), no collective"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes": f"{per_px} B per canvas px per launch"},
+        "hbm_frac_alg": B_ALG * value_canvas * 1e6 / (hbm_peak * 1e9),
+        "phase_ms_per_solve": {k: round(v, 4) for k, v in phases.items()},
+        "phase_launches_per_solve": nlaunch,
+        "plain": {"value": plain_value, "unit": UNIT, "images": plain_n,
+                  "batched_over_plain": value / world / plain_value},
+        "cpu_baseline": cpu, "parity_vs_oracle": parity,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "status_nonzero": sum(1 for s in st if s & ~gfd.STATUS_NONCONVERGED),
+        "nonconverged": sum(1 for s in st if s & gfd.STATUS_NONCONVERGED),
+        "clocks": clocks,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-images", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

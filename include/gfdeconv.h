@@ -1,0 +1,166 @@
+/*
+ * gfdeconv — guided-filter non-blind image deconvolution on one GB300 GPU.
+ *
+ * The method (Yang, Zhu, Zhang, Huang, arXiv 1609.01839):
+ *   observation model y = h * u_orig + gamma, circular convolution, i.i.d.
+ *   Gaussian noise of variance sigma^2 (Sec. 1, Eq. 1; h and sigma known);
+ *   Step 0 u_E = 0; then per iteration (Sec. 3.1, Steps 1-3):
+ *     lambda by the discrepancy principle (Sec. 3.2, Eq. 10-12),
+ *     u_I from Eq. 8 and u_p from Eq. 9 (FFT-domain solves of Eq. 6 and 7),
+ *     u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5), u_E <- u.
+ *
+ * Conventions for every entry point:
+ *   - Images are float32, row-major, M rows by N columns, with M and N powers
+ *     of two in [8, 4096] (the canvas; pad other sizes before calling).
+ *   - Buffers named "device" are CUDA device pointers on the context's device,
+ *     owned by the caller; the library never frees or retains them after the
+ *     call's stream work completes.  The library owns only its workspace.
+ *   - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t;
+ *     NULL = the legacy default stream) unless stated otherwise.  Argument
+ *     errors are returned synchronously, before any launch.  Conditions found
+ *     on the device (non-convergence, non-finite values, an invalid PSF) are
+ *     reported per image by gfdeconv_status() after the stream is synchronised.
+ *   - A context is not thread-safe: use one context per host thread / stream.
+ *   - Return value: GFD_OK (0) or a negative gfd_status code.
+ */
+#ifndef GFDECONV_H
+#define GFDECONV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfdeconv_ctx gfdeconv_ctx;
+
+typedef enum {
+  GFD_OK = 0,
+  GFD_ERR_INVALID_ARG = -1,      /* null pointer, bad w/eps/sigma/iters/PSF size */
+  GFD_ERR_UNSUPPORTED_SIZE = -2, /* M or N not a power of two in [8, 4096] */
+  GFD_ERR_NONFINITE_INPUT = -3,  /* non-finite scalar argument */
+  GFD_ERR_ALLOC = -4,            /* workspace allocation failed */
+  GFD_ERR_CUDA = -5,             /* a CUDA runtime call failed */
+  GFD_ERR_NONCONVERGED = -6,     /* (status) lambda root outside the bracket */
+  GFD_ERR_TIMEOUT = -7           /* reserved: no entry point waits on the device */
+} gfd_status;
+
+/* Per-image status bits returned by gfdeconv_status(). */
+#define GFD_STATUS_NONCONVERGED 1 /* Eq. 11 root not found inside [1e-14, inf) */
+#define GFD_STATUS_NONFINITE 2    /* a non-finite residual or lambda appeared */
+#define GFD_STATUS_BAD_PSF 4      /* sum of h <= 0 */
+#define GFD_STATUS_BAD_RHO 8      /* Eq. 12 radicand <= 0 */
+
+typedef struct {
+  /* Window statistics of the guided filter:
+   * 0 (default) = tile-shifted FP32 sums (the window mean of the guidance is
+   *   taken about a per-tile reference value, which removes the cancellation
+   *   in sigma_k^2 = E[I^2] - mu^2 for locally smooth content);
+   * 1 = plain FP32 sums (for the precision study). */
+  int var_precision;
+  /* rho of the discrepancy target (Sec. 3.2): <= 0 selects Eq. 12, else a
+   * fixed value in (0, 1]. */
+  double rho;
+  /* 1 (default): capture each solve as a CUDA graph and replay it when the
+   * same batch (pointers, sizes, parameters) is solved again. */
+  int use_graphs;
+} gfdeconv_opts;
+
+/* One image of a batched solve.  All pointers are device pointers. */
+typedef struct {
+  const float* y;   /* observation, M*N */
+  int M, N;         /* canvas, powers of two in [8, 4096] */
+  const float* h;   /* PSF, kh*kw row-major, centre at (kh/2, kw/2) */
+  int kh, kw;       /* odd, 1..255; a PSF larger than the canvas wraps around it */
+  double sigma;     /* noise std (Eq. 1), > 0 */
+  int w;            /* guided-filter window, odd, 1..17 */
+  double eps;       /* guided-filter regulariser (Eq. 3), > 0 */
+  float* u_out;     /* result u^K, M*N; also holds the iterate during the solve */
+  double* lambda_out; /* [iters] lambda_k (+inf: u_E in K, Sec. 3.2) or NULL */
+  double* isnr_out; /* [iters] ISNR of u^{k+1} in dB, needs u_orig, or NULL */
+  double* res_out;  /* [iters] ||h*u_E^k - y||^2 or NULL */
+  const float* u_orig; /* clean image for ISNR, M*N, or NULL */
+  const float* u_init; /* starting u_E (resume), M*N, or NULL for Step 0's 0 */
+  float* uI_out;    /* last iteration's u_I (Eq. 8), M*N, or NULL */
+  float* up_out;    /* last iteration's u_p (Eq. 9), M*N, or NULL */
+} gfdeconv_image;
+
+/* Create a context on `cuda_device` (opts NULL = defaults).  Allocates the
+ * twiddle and gradient-weight tables; workspaces grow on first use. */
+int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* opts);
+
+/* Destroy a context and free its workspace (synchronises the device). */
+void gfdeconv_destroy(gfdeconv_ctx* ctx);
+
+/* The whole method on one image (Sec. 3.1 Steps 0-3 with Sec. 3.2's lambda):
+ * `iters` iterations from u_E = 0 (or u_init), writing u^iters to u_out and
+ * the per-iteration lambda_k / ISNR_k when the arrays are given. */
+int gfdeconv_solve(gfdeconv_ctx* ctx, const float* y, int M, int N, const float* h,
+                   int kh, int kw, double sigma, int w, double eps, int iters,
+                   float* u_out, double* lambda_out, double* isnr_out,
+                   const float* u_orig, const float* u_init, void* stream);
+
+/* The same method on n independent images of possibly different sizes, run
+ * together: every phase of an iteration is one launch per distinct canvas
+ * size covering all images of that size.  `imgs` is a HOST array of n
+ * descriptors whose pointers are device pointers. */
+int gfdeconv_solve_batched(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
+                           int iters, void* stream);
+
+/* As gfdeconv_solve_batched, but every pointer in `imgs` is HOST memory
+ * (pinned memory recommended): inputs are copied to the device, the batch is
+ * solved, outputs are copied back, and the call returns after the stream has
+ * been synchronised. */
+int gfdeconv_solve_batched_host(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
+                                int iters, void* stream);
+
+/* u = guidfilter(I, p, w, eps) (Sec. 2, Eq. 3-5) with periodic windows:
+ * I guidance, p filtering input, all M*N device buffers. */
+int gfdeconv_guidfilter(gfdeconv_ctx* ctx, const float* I, const float* p, int M, int N,
+                        int w, double eps, float* u_out, void* stream);
+
+/* 2-D real DFT of x (M*N device) into the packed half spectrum X (device,
+ * M*(N/2) complex64 = M*N floats): X[m][l] = F(x)(m, l) for 1 <= l < N/2 and
+ * X[m][0] = F(x)(m, 0) + i F(x)(m, N/2).  The DFT diagonalises the circular
+ * operators of Sec. 3.1. */
+int gfdeconv_fft2_r2c(gfdeconv_ctx* ctx, const float* x, int M, int N, float* X, void* stream);
+
+/* Inverse of gfdeconv_fft2_r2c: x = (1/(M N)) * inverse DFT of the packed
+ * half spectrum X (a Hermitian spectrum is assumed). */
+int gfdeconv_fft2_c2r(gfdeconv_ctx* ctx, const float* X, int M, int N, float* x, void* stream);
+
+/* Per-image status bits (GFD_STATUS_*) of the last solve on this context.
+ * Synchronises the last solve's stream.  `n` entries are written. */
+int gfdeconv_status(gfdeconv_ctx* ctx, int* per_image_status, int n);
+
+/* Phases of a solve, for gfdeconv_solve_batched_timed. */
+#define GFD_NUM_PHASES 8
+#define GFD_PHASE_SETUP 0          /* statistics, rho, H = F(h), Y = F(y) (once) */
+#define GFD_PHASE_ROW_FWD 1        /* row pass of F(u_E) */
+#define GFD_PHASE_COL_FWD_LAMBDA 2 /* column pass of F(u_E) + first Eq. 11 pass */
+#define GFD_PHASE_LAMBDA_PASS 3    /* further Eq. 11 passes (skip when resolved) */
+#define GFD_PHASE_COL_SOLVE_INV 4  /* Eq. 8, 9 + inverse column passes */
+#define GFD_PHASE_ROW_INV 5        /* inverse row passes -> u_I, u_p */
+#define GFD_PHASE_GUIDED_FILTER 6  /* Eq. 3-5 (+ ISNR sums) */
+#define GFD_PHASE_COPY 7           /* memsets / device copies */
+
+/* Instrumentation: the same solve as gfdeconv_solve_batched, launched
+ * directly (no graph) with a CUDA event pair on `stream` around every launch.
+ * Adds each phase's summed device time in milliseconds to phase_ms[p] and its
+ * launch count to phase_launches[p] (host arrays of GFD_NUM_PHASES entries).
+ * Synchronises `stream` before returning. */
+int gfdeconv_solve_batched_timed(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
+                                 int iters, void* stream, double* phase_ms,
+                                 long long* phase_launches);
+
+/* Number of kernel launches the last solve issued (for instrumentation). */
+long long gfdeconv_last_launch_count(gfdeconv_ctx* ctx);
+
+/* Human-readable text for a gfd_status code (static storage). */
+const char* gfdeconv_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFDECONV_H */

@@ -1,0 +1,321 @@
+"""Guided-filter non-blind deconvolution (arXiv 1609.01839) on one GB300 GPU.
+
+Thin ctypes binding over the C-ABI library ``libgfdeconv.so`` (declared in
+``include/gfdeconv.h``).  This module only marshals arguments: every step of
+the method runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current CUDA stream.  There is no CPU fallback: importing the
+binding without the built library, or passing CPU tensors where device
+buffers are required, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+__all__ = [
+    "Context", "GfdError", "lib", "library_path", "header_functions",
+    "STATUS_NONCONVERGED", "STATUS_NONFINITE", "STATUS_BAD_PSF", "STATUS_BAD_RHO",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+HEADER = os.path.join(_ROOT, "include", "gfdeconv.h")
+library_path = os.path.join(_HERE, "libgfdeconv.so")
+
+STATUS_NONCONVERGED = 1
+STATUS_NONFINITE = 2
+STATUS_BAD_PSF = 4
+STATUS_BAD_RHO = 8
+NUM_PHASES = 8
+PHASES = ("setup", "row_fwd", "col_fwd_lambda", "lambda_pass", "col_solve_inv", "row_inv",
+          "guided_filter", "copy")
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/gfdeconv.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gfdeconv_\w+)\s*\(", text)))
+
+
+class GfdError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = _lib.gfdeconv_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+class Image(ctypes.Structure):
+    """Mirror of gfdeconv_image."""
+    _fields_ = [
+        ("y", ctypes.c_void_p), ("M", ctypes.c_int), ("N", ctypes.c_int),
+        ("h", ctypes.c_void_p), ("kh", ctypes.c_int), ("kw", ctypes.c_int),
+        ("sigma", ctypes.c_double), ("w", ctypes.c_int), ("eps", ctypes.c_double),
+        ("u_out", ctypes.c_void_p), ("lambda_out", ctypes.c_void_p),
+        ("isnr_out", ctypes.c_void_p), ("res_out", ctypes.c_void_p),
+        ("u_orig", ctypes.c_void_p), ("u_init", ctypes.c_void_p),
+        ("uI_out", ctypes.c_void_p), ("up_out", ctypes.c_void_p),
+    ]
+
+
+class Opts(ctypes.Structure):
+    """Mirror of gfdeconv_opts."""
+    _fields_ = [("var_precision", ctypes.c_int), ("rho", ctypes.c_double),
+                ("use_graphs", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(library_path):
+        raise ImportError(
+            f"{library_path} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    L = ctypes.CDLL(library_path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sigs = {
+        "gfdeconv_create": (ci, [ctypes.POINTER(vp), ci, ctypes.POINTER(Opts)]),
+        "gfdeconv_destroy": (None, [vp]),
+        "gfdeconv_solve": (ci, [vp, vp, ci, ci, vp, ci, ci, cd, ci, cd, ci, vp, vp, vp, vp, vp, vp]),
+        "gfdeconv_solve_batched": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp]),
+        "gfdeconv_solve_batched_host": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp]),
+        "gfdeconv_guidfilter": (ci, [vp, vp, vp, ci, ci, ci, cd, vp, vp]),
+        "gfdeconv_fft2_r2c": (ci, [vp, vp, ci, ci, vp, vp]),
+        "gfdeconv_fft2_c2r": (ci, [vp, vp, ci, ci, vp, vp]),
+        "gfdeconv_solve_batched_timed": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp,
+                                              ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_longlong)]),
+        "gfdeconv_status": (ci, [vp, ctypes.POINTER(ci), ci]),
+        "gfdeconv_last_launch_count": (ctypes.c_longlong, [vp]),
+        "gfdeconv_strerror": (ctypes.c_char_p, [ci]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+lib = _lib
+
+
+def _ptr(t, what, dtype=None, numel=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (there is no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _hptr(t, what, dtype=None, numel=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous host (CPU) tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (owns workspaces and cached
+    CUDA graphs).  Not thread-safe."""
+
+    def __init__(self, device: int = 0, var_precision: int = 0, rho: float = 0.0,
+                 use_graphs: bool = True):
+        import torch
+        torch.cuda.init()
+        self.device = device
+        self._h = ctypes.c_void_p()
+        opts = Opts(var_precision, rho, 1 if use_graphs else 0)
+        with torch.cuda.device(device):
+            rc = _lib.gfdeconv_create(ctypes.byref(self._h), device, ctypes.byref(opts))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_create")
+
+    def close(self):
+        if self._h:
+            _lib.gfdeconv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- entry points --------------------------------------------------------
+    def solve(self, y, h, sigma, w, eps, iters, u_orig=None, u_init=None, stream=None,
+              with_lambda=True, u_out=None):
+        """One image: returns (u, lambda[iters] float64, isnr[iters] or None)."""
+        import torch
+        M, N = y.shape
+        kh, kw = h.shape
+        u = torch.empty((M, N), dtype=torch.float32, device=y.device) if u_out is None else u_out
+        lam = torch.empty(max(iters, 1), dtype=torch.float64, device=y.device) if with_lambda else None
+        isnr = (torch.empty(max(iters, 1), dtype=torch.float64, device=y.device)
+                if u_orig is not None else None)
+        rc = _lib.gfdeconv_solve(
+            self._h, _ptr(y, "y", torch.float32), M, N, _ptr(h, "h", torch.float32), kh, kw,
+            float(sigma), int(w), float(eps), int(iters), _ptr(u, "u_out", torch.float32, M * N),
+            _ptr(lam, "lambda"), _ptr(isnr, "isnr"), _ptr(u_orig, "u_orig", torch.float32, M * N),
+            _ptr(u_init, "u_init", torch.float32, M * N), _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_solve")
+        return u, lam, isnr
+
+    def make_images(self, items, iters, want_res=False, want_uIp=False):
+        """Descriptors for solve_batched from dicts with CUDA tensors
+        y, h, sigma, w, eps and optional u_orig, u_init.  Allocates u (and
+        lambda / isnr / res / u_I / u_p) and stores them in each dict."""
+        import torch
+        arr = (Image * len(items))()
+        for i, it in enumerate(items):
+            y, h = it["y"], it["h"]
+            M, N = y.shape
+            dev = y.device
+            it["u"] = it.get("u") if it.get("u") is not None else torch.empty((M, N), dtype=torch.float32, device=dev)
+            it["lam"] = torch.empty(max(iters, 1), dtype=torch.float64, device=dev)
+            it["isnr"] = (torch.empty(max(iters, 1), dtype=torch.float64, device=dev)
+                          if it.get("u_orig") is not None else None)
+            it["res"] = torch.empty(max(iters, 1), dtype=torch.float64, device=dev) if want_res else None
+            if want_uIp:
+                it["uI"] = torch.empty((M, N), dtype=torch.float32, device=dev)
+                it["up"] = torch.empty((M, N), dtype=torch.float32, device=dev)
+            a = arr[i]
+            a.y = _ptr(y, "y", torch.float32)
+            a.M, a.N = M, N
+            a.h = _ptr(h, "h", torch.float32)
+            a.kh, a.kw = h.shape
+            a.sigma = float(it["sigma"])
+            a.w = int(it["w"])
+            a.eps = float(it["eps"])
+            a.u_out = _ptr(it["u"], "u", torch.float32, M * N)
+            a.lambda_out = _ptr(it["lam"], "lambda")
+            a.isnr_out = _ptr(it["isnr"], "isnr")
+            a.res_out = _ptr(it["res"], "res")
+            a.u_orig = _ptr(it.get("u_orig"), "u_orig", torch.float32, M * N)
+            a.u_init = _ptr(it.get("u_init"), "u_init", torch.float32, M * N)
+            a.uI_out = _ptr(it.get("uI"), "uI", torch.float32, M * N)
+            a.up_out = _ptr(it.get("up"), "up", torch.float32, M * N)
+        return arr
+
+    def solve_batched_images(self, arr, iters, stream=None):
+        rc = _lib.gfdeconv_solve_batched(self._h, len(arr), arr, int(iters), _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_solve_batched")
+
+    def solve_batched(self, items, iters, stream=None, want_res=False, want_uIp=False):
+        """Batched solve of dicts (see make_images); results land in the dicts."""
+        arr = self.make_images(items, iters, want_res, want_uIp)
+        self.solve_batched_images(arr, iters, stream)
+        return items
+
+    def make_host_images(self, items, iters):
+        """Descriptors for solve_batched_host from dicts of pinned CPU tensors
+        y, h (+ u_orig); allocates pinned outputs u, lam, isnr in the dicts."""
+        import torch
+        arr = (Image * len(items))()
+        for i, it in enumerate(items):
+            y, h = it["y"], it["h"]
+            M, N = y.shape
+            if it.get("u") is None:
+                it["u"] = torch.empty((M, N), dtype=torch.float32).pin_memory()
+            it["lam"] = torch.empty(max(iters, 1), dtype=torch.float64).pin_memory()
+            it["isnr"] = (torch.empty(max(iters, 1), dtype=torch.float64).pin_memory()
+                          if it.get("u_orig") is not None else None)
+            a = arr[i]
+            a.y = _hptr(y, "y", torch.float32)
+            a.M, a.N = M, N
+            a.h = _hptr(h, "h", torch.float32)
+            a.kh, a.kw = h.shape
+            a.sigma = float(it["sigma"])
+            a.w = int(it["w"])
+            a.eps = float(it["eps"])
+            a.u_out = _hptr(it["u"], "u", torch.float32)
+            a.lambda_out = _hptr(it["lam"], "lambda")
+            a.isnr_out = _hptr(it["isnr"], "isnr")
+            a.u_orig = _hptr(it.get("u_orig"), "u_orig", torch.float32)
+        return arr
+
+    def solve_batched_timed(self, arr, iters, stream=None):
+        """Direct-launch solve with an event pair around every launch; returns
+        (phase_ms[8], phase_launches[8]) summed over the solve."""
+        ms = (ctypes.c_double * NUM_PHASES)()
+        nl = (ctypes.c_longlong * NUM_PHASES)()
+        rc = _lib.gfdeconv_solve_batched_timed(self._h, len(arr), arr, int(iters), _stream(stream),
+                                               ms, nl)
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_solve_batched_timed")
+        return list(ms), list(nl)
+
+    def solve_batched_host_images(self, arr, iters, stream=None):
+        rc = _lib.gfdeconv_solve_batched_host(self._h, len(arr), arr, int(iters), _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_solve_batched_host")
+
+    def guidfilter(self, I, p, w, eps, stream=None, out=None):
+        import torch
+        M, N = I.shape
+        u = torch.empty_like(I) if out is None else out
+        rc = _lib.gfdeconv_guidfilter(self._h, _ptr(I, "I", torch.float32), _ptr(p, "p", torch.float32, M * N),
+                                      M, N, int(w), float(eps), _ptr(u, "u", torch.float32, M * N),
+                                      _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_guidfilter")
+        return u
+
+    def fft2_r2c(self, x, stream=None):
+        """Packed half spectrum as a complex64 (M, N/2) tensor."""
+        import torch
+        M, N = x.shape
+        X = torch.empty((M, N // 2), dtype=torch.complex64, device=x.device)
+        rc = _lib.gfdeconv_fft2_r2c(self._h, _ptr(x, "x", torch.float32), M, N, X.data_ptr(),
+                                    _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_fft2_r2c")
+        return X
+
+    def fft2_c2r(self, X, stream=None):
+        import torch
+        M, L = X.shape
+        x = torch.empty((M, 2 * L), dtype=torch.float32, device=X.device)
+        rc = _lib.gfdeconv_fft2_c2r(self._h, _ptr(X, "X", torch.complex64), M, 2 * L, x.data_ptr(),
+                                    _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_fft2_c2r")
+        return x
+
+    def status(self, n):
+        arr = (ctypes.c_int * n)()
+        rc = _lib.gfdeconv_status(self._h, arr, n)
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_status")
+        return list(arr)
+
+    def last_launch_count(self) -> int:
+        return int(_lib.gfdeconv_last_launch_count(self._h))

@@ -1,0 +1,743 @@
+// C-ABI of the guided-filter deconvolution library: argument validation,
+// workspace and plan management, launch sequencing and CUDA-graph replay.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "launch.h"
+
+using namespace gfd;
+
+namespace {
+
+constexpr int AUX_SLOTS = 8;
+
+struct Plan {
+  std::vector<unsigned char> key;
+  int n = 0, iters = 0;
+  std::vector<int> order;                // internal index -> user index
+  std::vector<ClassLaunch> classes;
+  std::vector<ImgDesc> h_imgs;           // internal order
+  std::vector<gfdeconv_image> user;      // internal order
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+};
+
+// Optional event pairs around every launch of record() (instrumentation).
+struct Timer {
+  std::vector<cudaEvent_t> ev;   // 2 per launch
+  std::vector<int> phase;
+  size_t used = 0;
+  cudaError_t begin(cudaStream_t s, int ph) {
+    if (2 * used + 2 > ev.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+      }
+    }
+    if (phase.size() <= used) phase.resize(used + 1);
+    phase[used] = ph;
+    return cudaEventRecord(ev[2 * used], s);
+  }
+  cudaError_t end(cudaStream_t s) {
+    const cudaError_t r = cudaEventRecord(ev[2 * used + 1], s);
+    ++used;
+    return r;
+  }
+  ~Timer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+struct AuxSlot {
+  ImgDesc* d_img = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool used = false;
+};
+
+}  // namespace
+
+struct gfdeconv_ctx {
+  int device = 0;
+  gfdeconv_opts opts{};
+  float2* tw = nullptr;
+  float* d2 = nullptr;
+  cudaStream_t cap = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  ImgDesc* d_imgs = nullptr;
+  ImgState* d_st = nullptr;
+  int cap_imgs = 0;
+  Plan plan;
+  bool have_plan = false;
+  cudaStream_t last_stream = nullptr;
+  long long last_launches = 0;
+  ImgState* aux_st = nullptr;
+  AuxSlot aux[AUX_SLOTS];
+  int aux_next = 0;
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace {
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+int map_err(cudaError_t e) {
+  if (e == cudaSuccess) return GFD_OK;
+  if (e == cudaErrorMemoryAllocation) return GFD_ERR_ALLOC;
+  return GFD_ERR_CUDA;
+}
+
+int validate_image(const gfdeconv_image& im, int iters) {
+  if (!im.y || !im.h || !im.u_out) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(im.M, 8, 4096) || !pow2_in(im.N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (im.kh < 1 || im.kw < 1 || im.kh > 255 || im.kw > 255 || !(im.kh & 1) || !(im.kw & 1))
+    return GFD_ERR_INVALID_ARG;
+  if (!std::isfinite(im.sigma) || !std::isfinite(im.eps)) return GFD_ERR_NONFINITE_INPUT;
+  if (!(im.sigma > 0.0) || !(im.eps > 0.0)) return GFD_ERR_INVALID_ARG;
+  if (im.w < 1 || im.w > 17 || !(im.w & 1)) return GFD_ERR_INVALID_ARG;
+  if (im.isnr_out && !im.u_orig) return GFD_ERR_INVALID_ARG;
+  if (iters < 0) return GFD_ERR_INVALID_ARG;
+  return GFD_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t image_ws_bytes(int M, int N) {
+  const size_t P = (size_t)M * N;
+  return 5 * align256(P * sizeof(float)) + 4 * align256((size_t)M * sizeof(float2));
+}
+
+cudaError_t ensure_ws(gfdeconv_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  if (c->ws) cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  e = cudaMalloc(&c->ws, bytes);
+  if (e != cudaSuccess) return e;
+  c->ws_bytes = bytes;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_imgs(gfdeconv_ctx* c, int n) {
+  if (n <= c->cap_imgs) return cudaSuccess;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  if (c->d_imgs) cudaFree(c->d_imgs);
+  if (c->d_st) cudaFree(c->d_st);
+  c->d_imgs = nullptr;
+  c->d_st = nullptr;
+  c->cap_imgs = 0;
+  if ((e = cudaMalloc(&c->d_imgs, sizeof(ImgDesc) * n)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_st, sizeof(ImgState) * n)) != cudaSuccess) return e;
+  c->cap_imgs = n;
+  return cudaSuccess;
+}
+
+std::vector<unsigned char> make_key(const gfdeconv_ctx* c, int n, const gfdeconv_image* imgs,
+                                    int iters) {
+  std::vector<unsigned char> k(sizeof(int) * 2 + sizeof(gfdeconv_opts) +
+                               sizeof(gfdeconv_image) * (size_t)n);
+  unsigned char* p = k.data();
+  std::memcpy(p, &n, sizeof(int));
+  p += sizeof(int);
+  std::memcpy(p, &iters, sizeof(int));
+  p += sizeof(int);
+  std::memcpy(p, &c->opts, sizeof(gfdeconv_opts));
+  p += sizeof(gfdeconv_opts);
+  std::memcpy(p, imgs, sizeof(gfdeconv_image) * (size_t)n);
+  return k;
+}
+
+void drop_plan(gfdeconv_ctx* c) {
+  if (c->plan.exec) cudaGraphExecDestroy(c->plan.exec);
+  c->plan = Plan();
+  c->have_plan = false;
+}
+
+cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters) {
+  Plan& pl = c->plan;
+  pl.n = n;
+  pl.iters = iters;
+  // group images by canvas, in order of first appearance
+  std::vector<std::pair<int, int>> sizes;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < n; ++i) {
+    const std::pair<int, int> sz(imgs[i].M, imgs[i].N);
+    size_t ci = 0;
+    while (ci < sizes.size() && sizes[ci] != sz) ++ci;
+    if (ci == sizes.size()) {
+      sizes.push_back(sz);
+      members.emplace_back();
+    }
+    members[ci].push_back(i);
+  }
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) total += image_ws_bytes(imgs[i].M, imgs[i].N);
+  cudaError_t e = ensure_ws(c, total);
+  if (e != cudaSuccess) return e;
+  if ((e = ensure_imgs(c, n)) != cudaSuccess) return e;
+  pl.order.clear();
+  pl.h_imgs.clear();
+  pl.user.clear();
+  pl.classes.clear();
+  char* cur = c->ws;
+  for (size_t ci = 0; ci < sizes.size(); ++ci) {
+    ClassLaunch cl{};
+    cl.cd.M = sizes[ci].first;
+    cl.cd.N = sizes[ci].second;
+    cl.cd.n_img = (int)members[ci].size();
+    cl.cd.img0 = (int)pl.order.size();
+    cl.imgs = c->d_imgs;
+    cl.st = c->d_st;
+    cl.max_rad = 0;
+    for (int ui : members[ci]) {
+      const gfdeconv_image& im = imgs[ui];
+      const size_t P = (size_t)im.M * im.N;
+      ImgDesc d{};
+      d.y = im.y;
+      d.h = im.h;
+      d.u = im.u_out;
+      d.uo = im.u_orig;
+      d.lam_out = im.lambda_out;
+      d.isnr_out = im.isnr_out;
+      d.res_out = im.res_out;
+      d.kh = im.kh;
+      d.kw = im.kw;
+      d.w = im.w;
+      d.sigma = im.sigma;
+      d.eps = im.eps;
+      d.rho_fixed = c->opts.rho;
+      float2** planes[5] = {&d.S, &d.QI, &d.Qp, &d.H, &d.Y};
+      for (float2** pp : planes) {
+        *pp = reinterpret_cast<float2*>(cur);
+        cur += align256(P * sizeof(float));
+      }
+      float2** cols[4] = {&d.H0, &d.HN, &d.Y0, &d.YN};
+      for (float2** pp : cols) {
+        *pp = reinterpret_cast<float2*>(cur);
+        cur += align256((size_t)im.M * sizeof(float2));
+      }
+      cl.max_rad = std::max(cl.max_rad, (im.w - 1) / 2);
+      pl.order.push_back(ui);
+      pl.h_imgs.push_back(d);
+      pl.user.push_back(im);
+    }
+    pl.classes.push_back(cl);
+  }
+  return cudaMemcpy(c->d_imgs, pl.h_imgs.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice);
+}
+
+#define GFD_CK(x)                            \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
+
+// Enqueue the whole solve: setup (a0), then Steps 1-3 for every iteration.
+// With a timer, every launch is bracketed by an event pair tagged by phase.
+#define GFD_T(ph, call)                                  \
+  do {                                                   \
+    if (tm) GFD_CK(tm->begin(s, ph));                    \
+    GFD_CK(call);                                        \
+    if (tm) GFD_CK(tm->end(s));                          \
+  } while (0)
+
+cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullptr) {
+  long long L = 0;
+  const Tables t{c->tw, c->d2};
+  const int plain = c->opts.var_precision == 1 ? 1 : 0;
+  GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(c->d_st, 0, sizeof(ImgState) * pl.n, s));
+  for (auto& cl : pl.classes) {
+    GFD_T(GFD_PHASE_SETUP, launch_setup_stats(cl, s));
+    ++L;
+  }
+  for (auto& cl : pl.classes) {
+    GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));
+    ++L;
+  }
+  for (auto& cl : pl.classes) {
+    GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_QI, s));
+    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_QI, SEL_S, false, s));
+    GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_H, false, s));
+    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_Y, SEL_S, false, s));
+    GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_YS, false, s));
+    GFD_T(GFD_PHASE_SETUP, launch_unpack_dc(cl, s));
+    L += 6;
+  }
+  for (int i = 0; i < pl.n; ++i) {
+    const gfdeconv_image& u = pl.user[i];
+    const size_t bytes = (size_t)u.M * u.N * sizeof(float);
+    if (u.u_init)
+      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.u_out, u.u_init, bytes, cudaMemcpyDeviceToDevice, s));
+    else
+      GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(u.u_out, 0, bytes, s));
+  }
+  for (int k = 0; k < pl.iters; ++k) {
+    for (auto& cl : pl.classes) {
+      GFD_T(GFD_PHASE_ROW_FWD, launch_row_r2c(cl, t, SEL_U, SEL_S, true, s));
+      GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
+      L += 2;
+    }
+    for (int p = 1; p <= LAMBDA_FALLBACK_PASSES; ++p)
+      for (auto& cl : pl.classes) {
+        GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == LAMBDA_FALLBACK_PASSES, s));
+        ++L;
+      }
+    for (auto& cl : pl.classes) {
+      GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
+      GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, 1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
+      GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
+      L += 3;
+    }
+  }
+  for (int i = 0; i < pl.n; ++i) {
+    const gfdeconv_image& u = pl.user[i];
+    const size_t bytes = (size_t)u.M * u.N * sizeof(float);
+    if (u.uI_out && pl.iters > 0)
+      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.uI_out, pl.h_imgs[i].QI, bytes, cudaMemcpyDeviceToDevice, s));
+    if (u.up_out && pl.iters > 0)
+      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.up_out, pl.h_imgs[i].Qp, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  pl.launches = L;
+  return cudaSuccess;
+}
+
+cudaError_t capture(gfdeconv_ctx* c, Plan& pl) {
+  GFD_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  const cudaError_t e = record(c, pl, c->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  if (e2 != cudaSuccess) return e2;
+  const cudaError_t e3 = cudaGraphInstantiate(&pl.exec, g, 0);
+  cudaGraphDestroy(g);
+  return e3;
+}
+
+// Reserve an aux slot (descriptor + workspace) for a single-image utility call.
+cudaError_t aux_slot(gfdeconv_ctx* c, size_t ws_bytes, AuxSlot** out) {
+  AuxSlot& a = c->aux[c->aux_next];
+  c->aux_next = (c->aux_next + 1) % AUX_SLOTS;
+  if (a.used) GFD_CK(cudaEventSynchronize(a.done));
+  if (!a.d_img) GFD_CK(cudaMalloc(&a.d_img, sizeof(ImgDesc)));
+  if (!a.done) GFD_CK(cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming));
+  if (ws_bytes > a.ws_bytes) {
+    if (a.ws) cudaFree(a.ws);
+    a.ws = nullptr;
+    a.ws_bytes = 0;
+    GFD_CK(cudaMalloc(&a.ws, ws_bytes));
+    a.ws_bytes = ws_bytes;
+  }
+  *out = &a;
+  return cudaSuccess;
+}
+
+cudaError_t aux_upload(AuxSlot* a, const ImgDesc& d, cudaStream_t s) {
+  return cudaMemcpyAsync(a->d_img, &d, sizeof(ImgDesc), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t aux_finish(AuxSlot* a, cudaStream_t s) {
+  a->used = true;
+  return cudaEventRecord(a->done, s);
+}
+
+int solve_batched_dev(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
+                      cudaStream_t s) {
+  std::vector<unsigned char> key = make_key(c, n, imgs, iters);
+  if (!(c->have_plan && c->plan.key == key)) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return map_err(e);
+    drop_plan(c);
+    e = build_plan(c, n, imgs, iters);
+    if (e != cudaSuccess) {
+      drop_plan(c);
+      return map_err(e);
+    }
+    if (c->opts.use_graphs) {
+      e = capture(c, c->plan);
+      if (e != cudaSuccess) {
+        drop_plan(c);
+        cudaGetLastError();
+        return map_err(e);
+      }
+    }
+    c->plan.key.swap(key);
+    c->have_plan = true;
+  }
+  cudaError_t e;
+  if (c->opts.use_graphs)
+    e = cudaGraphLaunch(c->plan.exec, s);
+  else
+    e = record(c, c->plan, s);
+  c->last_stream = s;
+  c->last_launches = c->plan.launches;
+  return map_err(e);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* gfdeconv_strerror(int code) {
+  switch (code) {
+    case GFD_OK: return "ok";
+    case GFD_ERR_INVALID_ARG: return "invalid argument";
+    case GFD_ERR_UNSUPPORTED_SIZE: return "unsupported size (M, N must be powers of two in [8, 4096])";
+    case GFD_ERR_NONFINITE_INPUT: return "non-finite scalar argument";
+    case GFD_ERR_ALLOC: return "device allocation failed";
+    case GFD_ERR_CUDA: return "CUDA runtime error";
+    case GFD_ERR_NONCONVERGED: return "regularisation parameter did not converge";
+    case GFD_ERR_TIMEOUT: return "timeout";
+    default: return "unknown error";
+  }
+}
+
+int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* opts) {
+  if (!out) return GFD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return GFD_ERR_CUDA;
+  if (cuda_device < 0 || cuda_device >= ndev) return GFD_ERR_INVALID_ARG;
+  if (opts && (opts->rho > 1.0 || !std::isfinite(opts->rho))) return GFD_ERR_INVALID_ARG;
+  if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return GFD_ERR_CUDA;
+  gfdeconv_ctx* c = new (std::nothrow) gfdeconv_ctx();
+  if (!c) return GFD_ERR_ALLOC;
+  c->device = cuda_device;
+  if (opts) {
+    c->opts = *opts;
+  } else {
+    c->opts.var_precision = 0;
+    c->opts.rho = 0.0;
+    c->opts.use_graphs = 1;
+  }
+  e = configure_kernels();
+  if (e != cudaSuccess) {
+    delete c;
+    return GFD_ERR_CUDA;
+  }
+  // twiddles W_4096^m and gradient weights 4 sin^2(pi m / 4096), in double, rounded once
+  std::vector<float2> tw(TW_N);
+  std::vector<float> d2(TW_N);
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < TW_N; ++m) {
+    const double th = 2.0 * pi * m / TW_N;
+    tw[m] = make_float2((float)std::cos(th), (float)-std::sin(th));
+    const double sn = std::sin(pi * m / TW_N);
+    d2[m] = (float)(4.0 * sn * sn);
+  }
+  if ((e = cudaMalloc(&c->tw, sizeof(float2) * TW_N)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d2, sizeof(float) * TW_N)) != cudaSuccess ||
+      (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * TW_N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d2, d2.data(), sizeof(float) * TW_N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMalloc(&c->aux_st, sizeof(ImgState))) != cudaSuccess ||
+      (e = cudaMemset(c->aux_st, 0, sizeof(ImgState))) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    gfdeconv_destroy(c);
+    return map_err(e);
+  }
+  *out = c;
+  return GFD_OK;
+}
+
+void gfdeconv_destroy(gfdeconv_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  drop_plan(c);
+  for (AuxSlot& a : c->aux) {
+    if (a.d_img) cudaFree(a.d_img);
+    if (a.ws) cudaFree(a.ws);
+    if (a.done) cudaEventDestroy(a.done);
+  }
+  if (c->tw) cudaFree(c->tw);
+  if (c->d2) cudaFree(c->d2);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_imgs) cudaFree(c->d_imgs);
+  if (c->d_st) cudaFree(c->d_st);
+  if (c->aux_st) cudaFree(c->aux_st);
+  if (c->stage) cudaFree(c->stage);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+int gfdeconv_solve_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
+                           void* stream) {
+  if (!c || !imgs || n <= 0) return GFD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int r = validate_image(imgs[i], iters);
+    if (r != GFD_OK) return r;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  return solve_batched_dev(c, n, imgs, iters, (cudaStream_t)stream);
+}
+
+int gfdeconv_solve_batched_timed(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
+                                 void* stream, double* phase_ms, long long* phase_launches) {
+  if (!c || !imgs || n <= 0 || !phase_ms || !phase_launches) return GFD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int r = validate_image(imgs[i], iters);
+    if (r != GFD_OK) return r;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // plan as the graph path would (the cached graph, if any, stays valid)
+  std::vector<unsigned char> key = make_key(c, n, imgs, iters);
+  if (!(c->have_plan && c->plan.key == key)) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return map_err(e);
+    drop_plan(c);
+    if ((e = build_plan(c, n, imgs, iters)) != cudaSuccess) {
+      drop_plan(c);
+      return map_err(e);
+    }
+    c->plan.key.swap(key);
+    c->have_plan = true;
+  }
+  Timer tm;
+  cudaError_t e = record(c, c->plan, s, &tm);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_err(e);
+  for (size_t i = 0; i < tm.used; ++i) {
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, tm.ev[2 * i], tm.ev[2 * i + 1])) != cudaSuccess)
+      return map_err(e);
+    const int ph = tm.phase[i];
+    if (ph >= 0 && ph < GFD_NUM_PHASES) {
+      phase_ms[ph] += ms;
+      phase_launches[ph] += 1;
+    }
+  }
+  c->last_stream = s;
+  c->last_launches = c->plan.launches;
+  return GFD_OK;
+}
+
+int gfdeconv_solve(gfdeconv_ctx* c, const float* y, int M, int N, const float* h, int kh, int kw,
+                   double sigma, int w, double eps, int iters, float* u_out, double* lambda_out,
+                   double* isnr_out, const float* u_orig, const float* u_init, void* stream) {
+  gfdeconv_image im{};
+  im.y = y;
+  im.M = M;
+  im.N = N;
+  im.h = h;
+  im.kh = kh;
+  im.kw = kw;
+  im.sigma = sigma;
+  im.w = w;
+  im.eps = eps;
+  im.u_out = u_out;
+  im.lambda_out = lambda_out;
+  im.isnr_out = isnr_out;
+  im.u_orig = u_orig;
+  im.u_init = u_init;
+  return gfdeconv_solve_batched(c, 1, &im, iters, stream);
+}
+
+int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
+                                void* stream) {
+  if (!c || !imgs || n <= 0) return GFD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int r = validate_image(imgs[i], iters);
+    if (r != GFD_OK) return r;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // device staging, one area per field, images back to back in user order
+  std::vector<size_t> off_y(n), off_h(n), off_uo(n), off_ui(n), off_u(n), off_l(n), off_is(n),
+      off_r(n), off_I(n), off_p(n);
+  size_t cur = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = cur;
+    cur += align256(bytes);
+    return o;
+  };
+  for (int i = 0; i < n; ++i) {
+    const gfdeconv_image& im = imgs[i];
+    const size_t P = (size_t)im.M * im.N * sizeof(float);
+    off_y[i] = take(P);
+    off_h[i] = take((size_t)im.kh * im.kw * sizeof(float));
+    off_uo[i] = im.u_orig ? take(P) : 0;
+    off_ui[i] = im.u_init ? take(P) : 0;
+    off_u[i] = take(P);
+    off_l[i] = im.lambda_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
+    off_is[i] = im.isnr_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
+    off_r[i] = im.res_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
+    off_I[i] = im.uI_out ? take(P) : 0;
+    off_p[i] = im.up_out ? take(P) : 0;
+  }
+  if (cur > c->stage_bytes) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return map_err(e);
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    if ((e = cudaMalloc(&c->stage, cur)) != cudaSuccess) return map_err(e);
+    c->stage_bytes = cur;
+  }
+  char* base = c->stage;
+  std::vector<gfdeconv_image> dev(imgs, imgs + n);
+  // host->device copies; runs that are contiguous on both sides are merged
+  struct Cp {
+    char* dst;
+    const char* src;
+    size_t bytes;
+  };
+  std::vector<Cp> h2d, d2h;
+  auto add = [](std::vector<Cp>& v, char* dst, const char* src, size_t bytes) {
+    if (!v.empty() && v.back().dst + v.back().bytes == dst && v.back().src + v.back().bytes == src)
+      v.back().bytes += bytes;
+    else
+      v.push_back(Cp{dst, src, bytes});
+  };
+  const int nf_in = 4;
+  for (int f = 0; f < nf_in; ++f)
+    for (int i = 0; i < n; ++i) {
+      const gfdeconv_image& im = imgs[i];
+      const size_t P = (size_t)im.M * im.N * sizeof(float);
+      if (f == 0) { dev[i].y = (const float*)(base + off_y[i]); add(h2d, base + off_y[i], (const char*)im.y, P); }
+      if (f == 1) { dev[i].h = (const float*)(base + off_h[i]); add(h2d, base + off_h[i], (const char*)im.h, (size_t)im.kh * im.kw * sizeof(float)); }
+      if (f == 2 && im.u_orig) { dev[i].u_orig = (const float*)(base + off_uo[i]); add(h2d, base + off_uo[i], (const char*)im.u_orig, P); }
+      if (f == 3 && im.u_init) { dev[i].u_init = (const float*)(base + off_ui[i]); add(h2d, base + off_ui[i], (const char*)im.u_init, P); }
+    }
+  for (int f = 0; f < 6; ++f)
+    for (int i = 0; i < n; ++i) {
+      const gfdeconv_image& im = imgs[i];
+      const size_t P = (size_t)im.M * im.N * sizeof(float);
+      const size_t it = sizeof(double) * (size_t)iters;
+      if (f == 0) { dev[i].u_out = (float*)(base + off_u[i]); add(d2h, (char*)im.u_out, base + off_u[i], P); }
+      if (f == 1 && im.lambda_out) { dev[i].lambda_out = (double*)(base + off_l[i]); if (it) add(d2h, (char*)im.lambda_out, base + off_l[i], it); }
+      if (f == 2 && im.isnr_out) { dev[i].isnr_out = (double*)(base + off_is[i]); if (it) add(d2h, (char*)im.isnr_out, base + off_is[i], it); }
+      if (f == 3 && im.res_out) { dev[i].res_out = (double*)(base + off_r[i]); if (it) add(d2h, (char*)im.res_out, base + off_r[i], it); }
+      if (f == 4 && im.uI_out) { dev[i].uI_out = (float*)(base + off_I[i]); add(d2h, (char*)im.uI_out, base + off_I[i], P); }
+      if (f == 5 && im.up_out) { dev[i].up_out = (float*)(base + off_p[i]); add(d2h, (char*)im.up_out, base + off_p[i], P); }
+    }
+  for (const Cp& cp : h2d) {
+    const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  const int r = solve_batched_dev(c, n, dev.data(), iters, s);
+  if (r != GFD_OK) return r;
+  for (const Cp& cp : d2h) {
+    const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  return map_err(cudaStreamSynchronize(s));
+}
+
+int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, int N, int w,
+                        double eps, float* u_out, void* stream) {
+  if (!c || !I || !p || !u_out) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (!std::isfinite(eps)) return GFD_ERR_NONFINITE_INPUT;
+  if (!(eps > 0.0) || w < 1 || w > 17 || !(w & 1)) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  AuxSlot* a = nullptr;
+  cudaError_t e = aux_slot(c, 0, &a);
+  if (e != cudaSuccess) return map_err(e);
+  ImgDesc d{};
+  d.QI = reinterpret_cast<float2*>(const_cast<float*>(I));
+  d.Qp = reinterpret_cast<float2*>(const_cast<float*>(p));
+  d.u = u_out;
+  d.w = w;
+  d.eps = eps;
+  if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
+  ClassLaunch cl{};
+  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.imgs = a->d_img;
+  cl.st = c->aux_st;
+  cl.max_rad = (w - 1) / 2;
+  if ((e = launch_guided_filter(cl, -1, c->opts.var_precision == 1 ? 1 : 0, s)) != cudaSuccess)
+    return map_err(e);
+  return map_err(aux_finish(a, s));
+}
+
+int gfdeconv_fft2_r2c(gfdeconv_ctx* c, const float* x, int M, int N, float* X, void* stream) {
+  if (!c || !x || !X) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)M * N;
+  AuxSlot* a = nullptr;
+  cudaError_t e = aux_slot(c, P * sizeof(float), &a);
+  if (e != cudaSuccess) return map_err(e);
+  ImgDesc d{};
+  d.u = const_cast<float*>(x);
+  d.S = reinterpret_cast<float2*>(a->ws);
+  d.Y = reinterpret_cast<float2*>(X);
+  if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
+  ClassLaunch cl{};
+  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.imgs = a->d_img;
+  cl.st = c->aux_st;
+  const Tables t{c->tw, c->d2};
+  if ((e = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s)) != cudaSuccess) return map_err(e);
+  if ((e = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s)) != cudaSuccess) return map_err(e);
+  return map_err(aux_finish(a, s));
+}
+
+int gfdeconv_fft2_c2r(gfdeconv_ctx* c, const float* X, int M, int N, float* x, void* stream) {
+  if (!c || !x || !X) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)M * N;
+  AuxSlot* a = nullptr;
+  cudaError_t e = aux_slot(c, P * sizeof(float), &a);
+  if (e != cudaSuccess) return map_err(e);
+  ImgDesc d{};
+  d.QI = reinterpret_cast<float2*>(a->ws);
+  if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
+  if ((e = cudaMemcpyAsync(a->ws, X, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return map_err(e);
+  ClassLaunch cl{};
+  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.imgs = a->d_img;
+  cl.st = c->aux_st;
+  const Tables t{c->tw, c->d2};
+  if ((e = launch_col_plain(cl, t, SEL_QI, SEL_QI, true, s)) != cudaSuccess) return map_err(e);
+  if ((e = launch_row_c2r(cl, t, SEL_QI, -1, 1.0f / ((float)M * (float)N), s)) != cudaSuccess)
+    return map_err(e);
+  if ((e = cudaMemcpyAsync(x, a->ws, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return map_err(e);
+  return map_err(aux_finish(a, s));
+}
+
+int gfdeconv_status(gfdeconv_ctx* c, int* per_image_status, int n) {
+  if (!c || !per_image_status || n < 0) return GFD_ERR_INVALID_ARG;
+  if (!c->have_plan) return GFD_ERR_INVALID_ARG;
+  if (n > c->plan.n) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return map_err(e);
+  std::vector<ImgState> st(c->plan.n);
+  e = cudaMemcpy(st.data(), c->d_st, sizeof(ImgState) * c->plan.n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return map_err(e);
+  std::vector<int> by_user(c->plan.n, 0);
+  for (int i = 0; i < c->plan.n; ++i) by_user[c->plan.order[i]] = st[i].status;
+  for (int i = 0; i < n; ++i) per_image_status[i] = by_user[i];
+  return GFD_OK;
+}
+
+long long gfdeconv_last_launch_count(gfdeconv_ctx* c) { return c ? c->last_launches : -1; }
+
+}  // extern "C"

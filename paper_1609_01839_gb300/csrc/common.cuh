@@ -1,0 +1,100 @@
+// Shared device helpers for the guided-filter deconvolution kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gfdeconv.h"
+
+#define GFD_HD __host__ __device__ __forceinline__
+#define GFD_D __device__ __forceinline__
+
+namespace gfd {
+
+// Twiddle table: W_4096^m = exp(-2 pi i m / 4096), m = 0..4095, computed on the
+// host in double and rounded once to float.  Any W_L^x with L | 4096 is
+// tw[x * (4096 / L)].
+constexpr int TW_LOG2 = 12;
+constexpr int TW_N = 1 << TW_LOG2;
+
+// Number of interpolation nodes for the regularisation-parameter equation
+// (Sec. 3.2, Eq. 11) evaluated per spectral pass.
+constexpr int KNODES = 12;
+// Fallback passes launched after the fused pass of each iteration.
+constexpr int LAMBDA_FALLBACK_PASSES = 4;
+constexpr double LAMBDA_LO = 1e-14;
+
+// status bits (per image)
+constexpr int ST_NONCONVERGED = 1;
+constexpr int ST_NONFINITE = 2;
+constexpr int ST_BAD_PSF = 4;
+constexpr int ST_BAD_RHO = 8;
+
+GFD_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+GFD_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+GFD_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+GFD_HD float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+GFD_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+GFD_HD float2 cmul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Per-image solver state, one per image of a batch, in device memory.
+struct ImgState {
+  double T;          // discrepancy target rho * P * sigma^2 (Sec. 3.2)
+  double rho;        // rho of Eq. 12 (or the fixed value)
+  double sum_y;      // sum of y   (= Y(0,0), kept in FP64)
+  double sum_yy;     // sum of y^2
+  double sum_h;      // sum of h   (= H(0,0))
+  double amax;       // (sum |h|)^2 >= max |H|^2
+  double den_isnr;   // ||y - u_orig||^2
+  double lam;        // lambda of the current iteration (inf: branch u_E in K)
+  double lo, hi;     // bracket of the nodes of the next pass
+  double lam_up;     // upper bound of the root from res and amax
+  double res;        // ||h*u_E - y||^2 of the current iteration
+  double acc[KNODES];// FP64 accumulators of sum w r t_j^2 at the nodes
+  double acc_res;    // FP64 accumulator of sum w r
+  double sum_u;      // FP64 sum of the current iterate u_E (its DC bin)
+  double d00;        // DC residual sum(h) sum(u_E) - sum(y), FP64
+  double err2;       // FP64 sum (u - u_orig)^2
+  float node[KNODES];// node values lambda_j (float) of the pending pass
+  unsigned int cta_done;   // last-block-done counter (spectral passes)
+  unsigned int gf_done;    // last-block-done counter (guided filter)
+  int need;          // 1: lambda unresolved, a fallback pass must run
+  int status;        // ST_* bits
+  int iter;          // iteration index of the pending outputs
+  int pad_;
+};
+
+// Per-image parameters and pointers, device memory.
+struct ImgDesc {
+  const float* y;     // M*N
+  const float* h;     // kh*kw
+  float* u;           // M*N, the iterate (caller's output buffer)
+  const float* uo;    // M*N or null
+  double* lam_out;    // [iters] or null
+  double* isnr_out;   // [iters] or null
+  double* res_out;    // [iters] or null
+  int kh, kw, w, pad_;
+  double sigma, eps, rho_fixed;
+  // workspace planes (M*N/2 complex each)
+  float2* S;          // forward spectrum scratch (row pass output, then U_E)
+  float2* QI;         // U_I, then u_I (real, in place)
+  float2* Qp;         // U_p, then u_p (real, in place)
+  float2* H;          // PSF spectrum (packed)
+  float2* Y;          // observation spectrum (packed)
+  float2* H0;         // H(k, 0),   k < M (unpacked DC column)
+  float2* HN;         // H(k, N/2)
+  float2* Y0;         // Y(k, 0)
+  float2* YN;         // Y(k, N/2)
+};
+
+// One size class of a batch: all images with the same canvas M x N.
+struct ClassDesc {
+  int M, N, n_img, img0;   // images img0 .. img0+n_img-1 of the batch
+};
+
+}  // namespace gfd

@@ -1,0 +1,179 @@
+// Power-of-two complex FFT on a team of threads, staged in shared memory.
+//
+// The transform X[k] = sum_n x[n] W_L^{nk}, W_L = exp(-2 pi i / L) (forward)
+// or with W_L^{-nk} (inverse, unnormalised), is computed by the mixed-radix
+// decimation-in-frequency recursion L = r_0 * L_1:
+//   X[i + r_0 k1] = sum_{n1} W_{L_1}^{n1 k1} [ W_L^{n1 i} sum_{n2} x[n1 + L_1 n2] W_{r_0}^{n2 i} ].
+// Stage s holds prod_{s'<s} r_{s'} independent sub-transforms of length L_s,
+// stored contiguously; a butterfly (g, j) loads the r_s elements
+// g*L_s + j + i*L_{s+1}, applies a radix-r_s DFT in registers and the twiddle
+// W_{L_s}^{j i}, and stores them back in place.  After the last stage X[k]
+// sits at the digit-reversed position out_pos(k).
+//
+// A team has L/R threads, each doing R/r_s butterflies per stage; all teams of
+// a block run the same L and synchronise with __syncthreads between stages.
+// Shared addresses are padded by one element per 16 (phys()) to spread banks.
+#pragma once
+#include "common.cuh"
+
+namespace gfd {
+
+constexpr int radix_for(int L) { return L >= 256 ? 16 : (L >= 64 ? 8 : (L >= 16 ? 4 : 2)); }
+
+constexpr int stage_radix(int L, int R, int s) {
+  int rem = L;
+  for (int i = 0; i < s; ++i) {
+    int r = rem < R ? rem : R;
+    rem /= r;
+  }
+  return rem < R ? rem : R;
+}
+constexpr int stage_len(int L, int R, int s) {
+  int rem = L;
+  for (int i = 0; i < s; ++i) {
+    int r = rem < R ? rem : R;
+    rem /= r;
+  }
+  return rem;
+}
+constexpr int num_stages(int L, int R) {
+  int n = 0, rem = L;
+  while (rem > 1) {
+    int r = rem < R ? rem : R;
+    rem /= r;
+    ++n;
+  }
+  return n;
+}
+
+GFD_HD int phys(int a) { return a + (a >> 4); }
+// elements of one team's buffer (odd, so that teams interleave across banks)
+GFD_HD int team_stride(int L) { return L + (L >> 4) + 1; }
+
+// cos / sin of 2 pi m / 16
+__device__ constexpr float kCos16[16] = {
+    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+__device__ constexpr float kSin16[16] = {
+    0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+    1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+    0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+    -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+
+// v * W_R^k (forward: exp(-2 pi i k/R); inverse: exp(+2 pi i k/R)), R <= 16
+template <int R, int k, bool INV>
+GFD_D float2 const_twiddle(float2 v) {
+  if constexpr (k == 0) {
+    return v;
+  } else if constexpr (4 * k == R) {
+    return cmul_mi<INV>(v);
+  } else {
+    constexpr int m = k * (16 / R);
+    const float c = kCos16[m];
+    const float s = INV ? kSin16[m] : -kSin16[m];
+    return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+  }
+}
+
+// In-register DFT of length R (natural-order input and output).
+template <int R, bool INV>
+struct DFT {
+  template <int k>
+  GFD_D static void combine(float2* x, const float2* e, const float2* o) {
+    if constexpr (k < R / 2) {
+      const float2 t = const_twiddle<R, k, INV>(o[k]);
+      x[k] = cadd(e[k], t);
+      x[k + R / 2] = csub(e[k], t);
+      combine<k + 1>(x, e, o);
+    }
+  }
+  GFD_D static void run(float2* x) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    DFT<R / 2, INV>::run(e);
+    DFT<R / 2, INV>::run(o);
+    combine<0>(x, e, o);
+  }
+};
+template <bool INV>
+struct DFT<1, INV> {
+  GFD_D static void run(float2*) {}
+};
+template <bool INV>
+struct DFT<2, INV> {
+  GFD_D static void run(float2* x) {
+    const float2 a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  }
+};
+
+GFD_D float2 twiddle(const float2* __restrict__ tw, int idx4096, bool inv) {
+  float2 w = __ldg(&tw[idx4096]);
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+template <int L, int R, bool INV, int s>
+struct Stage {
+  GFD_D static void run(float2* buf, int j, const float2* __restrict__ tw) {
+    constexpr int Ls = stage_len(L, R, s);
+    if constexpr (Ls > 1) {
+      constexpr int r = Ls < R ? Ls : R;
+      constexpr int Ln = Ls / r;
+      constexpr int T = L / R;
+      constexpr int twstep = TW_N / Ls;
+#pragma unroll
+      for (int q = 0; q < R / r; ++q) {
+        const int beta = j + T * q;
+        const int g = beta / Ln;
+        const int jj = beta % Ln;
+        const int base = g * Ls + jj;
+        float2 x[r];
+#pragma unroll
+        for (int i = 0; i < r; ++i) x[i] = buf[phys(base + i * Ln)];
+        DFT<r, INV>::run(x);
+        if constexpr (Ln > 1) {
+#pragma unroll
+          for (int i = 1; i < r; ++i) x[i] = cmul(x[i], twiddle(tw, jj * i * twstep, INV));
+        }
+#pragma unroll
+        for (int i = 0; i < r; ++i) buf[phys(base + i * Ln)] = x[i];
+      }
+      __syncthreads();
+      Stage<L, R, INV, s + 1>::run(buf, j, tw);
+    }
+  }
+};
+
+// Run the whole transform of one team (thread j of L/R) in place on buf.
+// Precondition: buf filled and a __syncthreads() issued by the caller.
+// Postcondition: X[k] at buf[phys(out_pos<L>(k))], block synchronised.
+template <int L, bool INV>
+GFD_D void fft_team(float2* buf, int j, const float2* __restrict__ tw) {
+  Stage<L, radix_for(L), INV, 0>::run(buf, j, tw);
+}
+
+// position of output k after the in-place stages (digit reversal)
+template <int L>
+GFD_D int out_pos(int k) {
+  constexpr int R = radix_for(L);
+  constexpr int S = num_stages(L, R);
+  int p = 0, rem = k;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int r = stage_radix(L, R, s);
+    const int Ln = stage_len(L, R, s) / r;
+    p += (rem % r) * Ln;
+    rem /= r;
+  }
+  return p;
+}
+
+}  // namespace gfd

@@ -1,0 +1,190 @@
+// Once-per-solve kernels: PSF embedding, observation statistics, the
+// discrepancy target (Sec. 3.2, Eq. 12) and the unpacked DC / Nyquist columns.
+#include "lambda.cuh"
+#include "launch.h"
+
+namespace gfd {
+
+GFD_D double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum y, y^2, (y - u_orig)^2 over each image (FP64), and sum h, sum |h|.
+// grid (chunks, n_img).
+__global__ void k_setup_stats(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st) {
+  __shared__ double red[3][32];
+  const int gi = cd.img0 + blockIdx.y;
+  const ImgDesc& d = imgs[gi];
+  const size_t P = (size_t)cd.M * cd.N;
+  double sy = 0.0, syy = 0.0, se = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = (double)d.y[i];
+    sy += v;
+    syy += v * v;
+    if (d.uo) {
+      const double e = v - (double)d.uo[i];
+      se += e * e;
+    }
+  }
+  sy = warp_sum_d(sy);
+  syy = warp_sum_d(syy);
+  se = warp_sum_d(se);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = sy;
+    red[1][warp] = syy;
+    red[2][warp] = se;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+    }
+    atomicAdd(&st[gi].sum_y, a);
+    atomicAdd(&st[gi].sum_yy, b);
+    if (d.uo) atomicAdd(&st[gi].den_isnr, c);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double sh = 0.0, sa = 0.0;
+    for (int i = 0; i < d.kh * d.kw; ++i) {
+      const double v = (double)d.h[i];
+      sh += v;
+      sa += fabs(v);
+    }
+    st[gi].sum_h = sh;
+    st[gi].amax = sa;  // squared in k_setup_init
+  }
+}
+
+// rho (Eq. 12), the target T = rho P sigma^2 (Sec. 3.2), the first bracket.
+__global__ void k_setup_init(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
+                             double rho_fixed) {
+  const int li = blockIdx.x * blockDim.x + threadIdx.x;
+  if (li >= cd.n_img) return;
+  const int gi = cd.img0 + li;
+  const ImgDesc& d = imgs[gi];
+  ImgState* S = st + gi;
+  const double P = (double)cd.M * cd.N;
+  const double sig2 = d.sigma * d.sigma;
+  const double h1 = S->amax;
+  S->amax = h1 * h1;
+  if (!(S->sum_h > 0.0)) S->status |= ST_BAD_PSF;
+  double rho;
+  if (rho_fixed > 0.0) {
+    rho = rho_fixed;
+  } else {
+    // ||y - mu(y)||^2 = sum y^2 - (sum y)^2 / P
+    const double num = (S->sum_yy - S->sum_y * S->sum_y / P) - P * sig2;
+    const double den = h1 * h1 * S->sum_yy;
+    const double rad = 1.0 - num / den;
+    if (rad > 0.0) {
+      rho = fmin(1.0, sqrt(rad));
+    } else {
+      S->status |= ST_BAD_RHO;
+      rho = 1.0;
+    }
+  }
+  S->rho = rho;
+  S->T = rho * P * sig2;
+  S->lam = NAN;
+  S->need = 0;
+  set_bracket(S, INITIAL_LO, INITIAL_HI);
+}
+
+// Circular PSF embedding: offset (a - kh/2, b - kw/2) -> canvas index mod (M, N).
+__global__ void k_embed_psf(ClassDesc cd, const ImgDesc* __restrict__ imgs, int dst_sel) {
+  const size_t P = (size_t)cd.M * cd.N;
+  const size_t total = P * cd.n_img;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int li = (int)(idx / P);
+    const int rem = (int)(idx - (size_t)li * P);
+    const int i = rem / cd.N, j = rem - i * cd.N;
+    const ImgDesc& d = imgs[cd.img0 + li];
+    const int rh = d.kh / 2, rw = d.kw / 2;
+    float s = 0.0f;
+    for (int a = (i + rh) % cd.M; a < d.kh; a += cd.M)
+      for (int b = (j + rw) % cd.N; b < d.kw; b += cd.N) s += d.h[a * d.kw + b];
+    float* dst = dst_sel == SEL_QI ? reinterpret_cast<float*>(d.QI) : reinterpret_cast<float*>(d.S);
+    dst[rem] = s;
+  }
+}
+
+// Unpack column 0 of the packed H and Y into the bins (k, 0) and (k, N/2);
+// the DC bins take the FP64 sums (rounded once).
+__global__ void k_unpack_dc(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st) {
+  const int gi = cd.img0 + blockIdx.y;
+  const ImgDesc& d = imgs[gi];
+  const int M = cd.M, Lc = cd.N / 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const int km = (M - k) & (M - 1);
+  const float2 hk = d.H[(size_t)k * Lc], hm = d.H[(size_t)km * Lc];
+  const float2 yk = d.Y[(size_t)k * Lc], ym = d.Y[(size_t)km * Lc];
+  float2 A, B;
+  {
+    const float2 c = cconj(hm);
+    A = cscale(cadd(hk, c), 0.5f);
+    const float2 D = csub(hk, c);
+    B = make_float2(0.5f * D.y, -0.5f * D.x);
+  }
+  if (k == 0) A = make_float2((float)st[gi].sum_h, 0.0f);
+  d.H0[k] = A;
+  d.HN[k] = B;
+  {
+    const float2 c = cconj(ym);
+    A = cscale(cadd(yk, c), 0.5f);
+    const float2 D = csub(yk, c);
+    B = make_float2(0.5f * D.y, -0.5f * D.x);
+  }
+  if (k == 0) A = make_float2((float)st[gi].sum_y, 0.0f);
+  d.Y0[k] = A;
+  d.YN[k] = B;
+  if (k == 0) {
+    d.H[0].x = (float)st[gi].sum_h;
+    d.Y[0].x = (float)st[gi].sum_y;
+  }
+}
+
+cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
+  const size_t P = (size_t)c.cd.M * c.cd.N;
+  int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));
+  if (chunks > 64) chunks = 64;
+  k_setup_stats<<<dim3(chunks, c.cd.n_img), 256, 0, s>>>(c.cd, c.imgs, c.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s) {
+  k_setup_init<<<(c.cd.n_img + 127) / 128, 128, 0, s>>>(c.cd, c.imgs, c.st, rho_fixed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_embed_psf(const ClassLaunch& c, int dst, cudaStream_t s) {
+  const size_t total = (size_t)c.cd.M * c.cd.N * c.cd.n_img;
+  size_t nb = (total + 255) / 256;
+  if (nb > 152 * 64) nb = 152 * 64;
+  k_embed_psf<<<(unsigned)nb, 256, 0, s>>>(c.cd, c.imgs, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s) {
+  k_unpack_dc<<<dim3((c.cd.M + 127) / 128, c.cd.n_img), 128, 0, s>>>(c.cd, c.imgs, c.st);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_fft_kernels();
+cudaError_t configure_gf_kernel();
+
+cudaError_t configure_kernels() {
+  cudaError_t e = configure_fft_kernels();
+  if (e != cudaSuccess) return e;
+  return configure_gf_kernel();
+}
+
+}  // namespace gfd

@@ -1,0 +1,62 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gfd {
+
+enum PlaneSel : int {
+  SEL_Y = 0,   // observation (real)
+  SEL_U = 1,   // iterate / output (real)
+  SEL_S = 2,   // spectrum scratch
+  SEL_QI = 3,  // U_I then u_I
+  SEL_QP = 4,  // U_p then u_p
+  SEL_H = 5,   // PSF spectrum
+  SEL_YS = 6,  // observation spectrum
+};
+
+struct Tables {
+  const float2* tw;   // W_4096^m
+  const float* d2;    // 4 sin^2(pi m / 4096)
+};
+
+// Everything a launch needs about one size class.
+struct ClassLaunch {
+  ClassDesc cd;
+  const ImgDesc* imgs;  // device array (whole batch)
+  ImgState* st;         // device array (whole batch)
+  int max_rad;          // largest guided-filter radius in the class
+};
+
+// Row pass of the 2-D real DFT: real plane src -> packed rows dst.
+// do_sum: accumulate the FP64 sum of src into st.sum_u.
+cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst,
+                           bool do_sum, cudaStream_t s);
+// Inverse row pass, in place on one or two planes (sel1 < 0: one plane).
+cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1,
+                           float scale, cudaStream_t s);
+// Plain column FFT src -> dst (in place allowed), forward or inverse.
+cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst,
+                             bool inverse, cudaStream_t s);
+// Forward column FFT of S in place fused with the first lambda pass.
+cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter,
+                                  cudaStream_t s);
+// Fallback lambda pass over the stored spectrum (exits early where resolved).
+cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
+                               cudaStream_t s);
+// Spectral solves (Eq. 8, 9) fused with the inverse column FFTs: S -> QI, Qp.
+cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s);
+// Guided filter (Eq. 3-5): (QI, Qp) real planes -> u.  iter < 0: no ISNR.
+cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var,
+                                 cudaStream_t s);
+// Setup kernels.
+cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s);
+cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s);
+cudaError_t launch_embed_psf(const ClassLaunch& c, int dst, cudaStream_t s);
+cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s);
+
+// Opt every kernel into large dynamic shared memory (once per process/device).
+cudaError_t configure_kernels();
+
+}  // namespace gfd

@@ -1,0 +1,318 @@
+"""GPU parity: every step of the CUDA path, called through the C-ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances (written here, derived in the design doc):
+  u          max-abs 2e-5 on [0, 1] images, per iteration
+  lambda     1e-6 relative on a teacher-forced step (the GPU step fed the
+             oracle's own u_E^k); along a free trajectory the GPU's u_E drifts
+             from the oracle's by up to ~1e-6, which moves lambda by more, so
+             free-trajectory lambda is held to 1e-4 relative
+  ISNR       0.01 dB
+  FFT        relative rms error 1e-6 of the spectrum's norm
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+import synthetic as S  # noqa: E402
+import paper_1609_01839_gb300 as gfd  # noqa: E402
+
+DEV = torch.device("cuda:0")
+U_TOL = 2e-5
+LAM_TOL_TF = 1e-6
+LAM_TOL_FREE = 1e-4
+ISNR_TOL = 0.01
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gfd.Context(0)
+    yield c
+    c.close()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# 2-D real DFT (Sec. 3.1's diagonalisation)
+# ---------------------------------------------------------------------------
+
+def packed_ref(x):
+    F = np.fft.fft2(x.astype(np.float64))
+    M, N = x.shape
+    P = F[:, : N // 2].copy()
+    P[:, 0] = F[:, 0] + 1j * F[:, N // 2]
+    return P
+
+
+@pytest.mark.parametrize("M,N", [(8, 8), (16, 32), (64, 16), (32, 128), (256, 256),
+                                 (512, 1024), (1024, 512), (4096, 64), (64, 4096), (2048, 2048)])
+def test_fft2_r2c_matches_dft(ctx, M, N):
+    rng = np.random.default_rng(M * 7 + N)
+    x = rng.random((M, N)).astype(np.float32)
+    X = host(ctx.fft2_r2c(cuda(x))).astype(np.complex128)
+    ref = packed_ref(x)
+    rel = np.linalg.norm(X - ref) / np.linalg.norm(ref)
+    assert rel < 1e-6, rel
+    # c2r inverts it
+    back = host(ctx.fft2_c2r(cuda(ref.astype(np.complex64))))
+    assert np.abs(back - x).max() < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# Guided filter (Sec. 2, Eq. 3-5)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,w,eps", [(8, 8, 9, 1e-3), (16, 32, 3, 1e-3), (64, 64, 1, 1e-3),
+                                       (64, 128, 5, 1e-3), (256, 256, 7, 1e-3),
+                                       (256, 512, 9, 1e-4), (128, 128, 17, 1e-2),
+                                       (32, 2048, 11, 1e-3)])
+def test_guided_filter_matches_oracle(ctx, M, N, w, eps):
+    rng = np.random.default_rng(M + N + w)
+    u0 = S.image_polygons(3, M, N, n_poly=8, texture_std=0.02, rng=rng)
+    I = (u0 + 0.01 * rng.standard_normal((M, N))).astype(np.float32)
+    p = (u0 + 0.03 * rng.standard_normal((M, N))).astype(np.float32)
+    got = host(ctx.guidfilter(cuda(I), cuda(p), w, eps))
+    ref = O.guided_filter(I, p, w, eps)
+    assert np.abs(got - ref).max() < U_TOL
+
+
+def test_guided_filter_constant_fixed_point(ctx):
+    c = torch.full((64, 64), 0.37, device=DEV)
+    out = host(ctx.guidfilter(c, c, 7, 1e-3))
+    assert np.abs(out - 0.37).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Teacher-forced single iterations: the GPU step from the oracle's u_E^k
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c0_trace():
+    p = S.config_c0()
+    return p, O.solve(p.y, p.h, p.sigma, p.w, p.eps, p.iters, u_orig=p.u_orig, trace=True)
+
+
+@pytest.fixture(scope="module")
+def c1_trace():
+    p = S.config_c1()
+    return p, O.solve(p.y, p.h, p.sigma, p.w, p.eps, p.iters, u_orig=p.u_orig, trace=True)
+
+
+def gpu_step(ctx, p, uE):
+    items = [{"y": cuda(p.y), "h": cuda(p.h), "sigma": p.sigma, "w": p.w, "eps": p.eps,
+              "u_init": cuda(uE.astype(np.float32))}]
+    ctx.solve_batched(items, 1, want_res=True, want_uIp=True)
+    torch.cuda.synchronize()
+    it = items[0]
+    return (float(host(it["lam"])[0]), float(host(it["res"])[0]), host(it["u"]),
+            host(it["uI"]), host(it["up"]))
+
+
+def oracle_step(p, uE):
+    M, N = p.shape
+    H = O.psf_spectrum(p.h, M, N)
+    Y = np.fft.fft2(p.y.astype(np.float64))
+    T = O.discrepancy_target(p.y, p.h, p.sigma)
+    uE32 = uE.astype(np.float32).astype(np.float64)
+    return O.iterate(H, Y, O.grad_weight(M, N), uE32, T, p.w, p.eps)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 9])
+def test_teacher_forced_step_c0(ctx, c0_trace, k):
+    p, tr = c0_trace
+    lam, res, u, uI, up = gpu_step(ctx, p, tr["uE"][k])
+    ref = oracle_step(p, tr["uE"][k])
+    assert res == pytest.approx(ref["res"], rel=1e-6)
+    if math.isinf(ref["lam"]):
+        assert math.isinf(lam)
+    else:
+        assert abs(lam / ref["lam"] - 1) < LAM_TOL_TF, (lam, ref["lam"])
+    assert np.abs(up - ref["up"]).max() < U_TOL
+    assert np.abs(uI - ref["uI"]).max() < U_TOL
+    assert np.abs(u - ref["u"]).max() < U_TOL
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 10, 19])
+def test_teacher_forced_step_c1(ctx, c1_trace, k):
+    p, tr = c1_trace
+    lam, res, u, uI, up = gpu_step(ctx, p, tr["uE"][k])
+    ref = oracle_step(p, tr["uE"][k])
+    assert res == pytest.approx(ref["res"], rel=1e-6)
+    assert abs(lam / ref["lam"] - 1) < LAM_TOL_TF, (lam, ref["lam"])
+    assert np.abs(u - ref["u"]).max() < U_TOL
+
+
+# ---------------------------------------------------------------------------
+# Free trajectories of the whole method (Steps 0-3)
+# ---------------------------------------------------------------------------
+
+def check_trajectory(ctx, p, tr, iters):
+    u, lam, isnr = ctx.solve(cuda(p.y), cuda(p.h), p.sigma, p.w, p.eps, iters,
+                             u_orig=cuda(p.u_orig))
+    torch.cuda.synchronize()
+    lam, isnr, u = host(lam), host(isnr), host(u)
+    for k in range(iters):
+        if math.isinf(tr["lam"][k]):
+            assert math.isinf(lam[k])
+        else:
+            assert abs(lam[k] / tr["lam"][k] - 1) < LAM_TOL_FREE, (k, lam[k], tr["lam"][k])
+        assert abs(isnr[k] - tr["isnr"][k]) < ISNR_TOL, (k, isnr[k], tr["isnr"][k])
+    assert np.abs(u - tr["u"]).max() < U_TOL
+    assert ctx.status(1)[0] & ~gfd.STATUS_NONCONVERGED == 0
+
+
+def test_trajectory_c0(ctx, c0_trace):
+    p, tr = c0_trace
+    check_trajectory(ctx, p, tr, p.iters)
+
+
+def test_trajectory_c1(ctx, c1_trace):
+    p, tr = c1_trace
+    check_trajectory(ctx, p, tr, p.iters)
+
+
+def test_every_iterate_c0(ctx, c0_trace):
+    """u^k within tolerance at every iteration k (solves of 1..K iterations)."""
+    p, tr = c0_trace
+    for k in range(1, p.iters + 1):
+        u, _, _ = ctx.solve(cuda(p.y), cuda(p.h), p.sigma, p.w, p.eps, k)
+        torch.cuda.synchronize()
+        assert np.abs(host(u) - tr["u_k"][k - 1]).max() < U_TOL, k
+
+
+# ---------------------------------------------------------------------------
+# Batched execution (uneven sizes) equals the plain path and the oracle
+# ---------------------------------------------------------------------------
+
+def c2_subset():
+    # images of every canvas / PSF / window class, in index order
+    return [S.config_c2_image(i, iters=15) for i in (0, 1, 2, 3, 4, 5, 6, 7)]
+
+
+def test_batched_equals_plain_and_oracle(ctx):
+    probs = c2_subset()
+    iters = 4
+    items = [{"y": cuda(p.y), "h": cuda(p.h), "sigma": p.sigma, "w": p.w, "eps": p.eps,
+              "u_orig": cuda(p.u_orig)} for p in probs]
+    ctx.solve_batched(items, iters)
+    torch.cuda.synchronize()
+    for p, it in zip(probs, items):
+        u1, lam1, isnr1 = ctx.solve(cuda(p.y), cuda(p.h), p.sigma, p.w, p.eps, iters,
+                                    u_orig=cuda(p.u_orig))
+        torch.cuda.synchronize()
+        assert np.abs(host(it["u"]) - host(u1)).max() < 1e-6
+        assert np.allclose(host(it["lam"]), host(lam1), rtol=1e-9)
+    for p, it in list(zip(probs, items))[:4]:
+        ref = O.solve(p.y, p.h, p.sigma, p.w, p.eps, iters, u_orig=p.u_orig)
+        assert np.abs(host(it["u"]) - ref["u"]).max() < U_TOL
+        np.testing.assert_allclose(host(it["isnr"]), ref["isnr"], atol=ISNR_TOL)
+
+
+def test_batched_host_entry_point(ctx):
+    probs = c2_subset()[:3]
+    iters = 3
+    dev_items = [{"y": cuda(p.y), "h": cuda(p.h), "sigma": p.sigma, "w": p.w, "eps": p.eps,
+                  "u_orig": cuda(p.u_orig)} for p in probs]
+    ctx.solve_batched(dev_items, iters)
+    torch.cuda.synchronize()
+    host_items = [{"y": torch.from_numpy(p.y).pin_memory(), "h": torch.from_numpy(p.h).pin_memory(),
+                   "sigma": p.sigma, "w": p.w, "eps": p.eps,
+                   "u_orig": torch.from_numpy(p.u_orig).pin_memory()} for p in probs]
+    arr = ctx.make_host_images(host_items, iters)
+    ctx.solve_batched_host_images(arr, iters)
+    for d, h in zip(dev_items, host_items):
+        assert np.abs(host(d["u"]) - h["u"].numpy()).max() < 1e-6
+        np.testing.assert_allclose(h["isnr"].numpy(), host(d["isnr"]), atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+
+def test_lambda_infinite_branch(ctx):
+    """sigma so large that u_E = 0 already meets the discrepancy bound:
+    lambda = inf (Sec. 3.2) and u stays 0 (guidfilter(0, 0) = 0)."""
+    p = S.config_c0(M=32, N=32)
+    sigma = 10.0
+    ref = O.solve(p.y, p.h, sigma, p.w, p.eps, 2)
+    assert all(math.isinf(l) for l in ref["lam"])
+    u, lam, _ = ctx.solve(cuda(p.y), cuda(p.h), sigma, p.w, p.eps, 2)
+    torch.cuda.synchronize()
+    assert np.all(np.isinf(host(lam)))
+    assert np.abs(host(u) - ref["u"]).max() < 1e-7
+
+
+@pytest.mark.parametrize("M,N,w,k", [(8, 8, 9, 3), (8, 16, 3, 5), (16, 64, 5, 9), (128, 32, 7, 15)])
+def test_small_and_nonsquare(ctx, M, N, w, k):
+    rng = np.random.default_rng(M * N + w)
+    u0 = S.image_polygons(11, M, N, n_poly=3, texture_std=0.02, rng=rng)
+    h = S.psf_gaussian(k, 1.2)
+    yb = S.blur_circular(u0, h)
+    sigma = 0.01
+    y = (yb + sigma * rng.standard_normal((M, N))).astype(np.float32)
+    h32 = h.astype(np.float32)
+    ref = O.solve(y, h32, sigma, w, 1e-3, 3)
+    u, lam, _ = ctx.solve(cuda(y), cuda(h32), sigma, w, 1e-3, 3)
+    torch.cuda.synchronize()
+    assert np.abs(host(u) - ref["u"]).max() < U_TOL
+    for a, b in zip(host(lam), ref["lam"]):
+        assert (math.isinf(a) and math.isinf(b)) or abs(a / b - 1) < LAM_TOL_FREE
+
+
+def test_zero_iterations_returns_start(ctx):
+    p = S.config_c0(M=64, N=64)
+    u0 = np.full((64, 64), 0.25, dtype=np.float32)
+    u, _, _ = ctx.solve(cuda(p.y), cuda(p.h), p.sigma, p.w, p.eps, 0, u_init=cuda(u0))
+    torch.cuda.synchronize()
+    assert np.all(host(u) == 0.25)
+
+
+def test_invalid_arguments_rejected(ctx):
+    y = torch.zeros((64, 64), device=DEV)
+    h = torch.ones((3, 3), device=DEV) / 9
+    with pytest.raises(gfd.GfdError) as e:
+        ctx.solve(torch.zeros((48, 64), device=DEV), h, 0.01, 3, 1e-3, 1)
+    assert e.value.code == -2
+    with pytest.raises(gfd.GfdError) as e:
+        ctx.solve(y, h, 0.01, 4, 1e-3, 1)          # even window
+    assert e.value.code == -1
+    with pytest.raises(gfd.GfdError) as e:
+        ctx.solve(y, h, 0.01, 3, -1.0, 1)          # eps <= 0
+    assert e.value.code == -1
+    with pytest.raises(gfd.GfdError) as e:
+        ctx.solve(y, h, float("nan"), 3, 1e-3, 1)  # non-finite sigma
+    assert e.value.code == -3
+    with pytest.raises(gfd.GfdError):
+        ctx.solve(y, torch.ones((2, 3), device=DEV), 0.01, 3, 1e-3, 1)  # even PSF
+    with pytest.raises(ValueError):
+        ctx.solve(y.cpu(), h, 0.01, 3, 1e-3, 1)    # no CPU path
+
+
+def test_bad_psf_reported_in_status(ctx):
+    y = torch.rand((32, 32), device=DEV)
+    h = -torch.ones((3, 3), device=DEV) / 9
+    ctx.solve(y, h, 0.01, 3, 1e-3, 1)
+    st = ctx.status(1)[0]
+    assert st & gfd.STATUS_BAD_PSF
+
+
+def test_launch_count_reported(ctx):
+    p = S.config_c0(M=64, N=64)
+    ctx.solve(cuda(p.y), cuda(p.h), p.sigma, p.w, p.eps, 2)
+    torch.cuda.synchronize()
+    assert ctx.last_launch_count() > 10
