@@ -156,6 +156,10 @@ int gfdeconv_solve_batched_timed(gfdeconv_ctx* ctx, int n, const gfdeconv_image*
 /* Number of kernel launches the last solve issued (for instrumentation). */
 long long gfdeconv_last_launch_count(gfdeconv_ctx* ctx);
 
+/* Text of the last CUDA runtime error behind a GFD_ERR_CUDA / GFD_ERR_ALLOC
+ * return on this host thread ("no error" if none; static storage). */
+const char* gfdeconv_last_cuda_error(void);
+
 /* Human-readable text for a gfd_status code (static storage). */
 const char* gfdeconv_strerror(int code);
 

@@ -42,6 +42,8 @@ def header_functions() -> list[str]:
 class GfdError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         msg = _lib.gfdeconv_strerror(code).decode() if _lib is not None else str(code)
+        if _lib is not None and code in (-4, -5):
+            msg += " [" + _lib.gfdeconv_last_cuda_error().decode() + "]"
         super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
         self.code = code
 
@@ -86,6 +88,7 @@ def _load():
         "gfdeconv_status": (ci, [vp, ctypes.POINTER(ci), ci]),
         "gfdeconv_last_launch_count": (ctypes.c_longlong, [vp]),
         "gfdeconv_strerror": (ctypes.c_char_p, [ci]),
+        "gfdeconv_last_cuda_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)

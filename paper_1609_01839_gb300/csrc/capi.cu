@@ -91,8 +91,11 @@ namespace {
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 int map_err(cudaError_t e) {
   if (e == cudaSuccess) return GFD_OK;
+  g_last_cuda_error = e;
   if (e == cudaErrorMemoryAllocation) return GFD_ERR_ALLOC;
   return GFD_ERR_CUDA;
 }
@@ -739,5 +742,9 @@ int gfdeconv_status(gfdeconv_ctx* c, int* per_image_status, int n) {
 }
 
 long long gfdeconv_last_launch_count(gfdeconv_ctx* c) { return c ? c->last_launches : -1; }
+
+const char* gfdeconv_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no error" : cudaGetErrorString(g_last_cuda_error);
+}
 
 }  // extern "C"

@@ -42,6 +42,18 @@ GFD_HD float2 cmul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// Sum over the threads of a warp.  Blocks smaller than a warp (tiny images)
+// have blockDim a power of two < 32: the mask and offsets stay inside it.
+GFD_D float warp_sum(float v) {
+  const unsigned int n = blockDim.x < 32 ? blockDim.x : 32u;
+  const unsigned int mask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    if ((unsigned)o < n) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+GFD_D int num_warps() { return (int)((blockDim.x + 31) >> 5); }
+
 // Per-image solver state, one per image of a batch, in device memory.
 struct ImgState {
   double T;          // discrepancy target rho * P * sigma^2 (Sec. 3.2)

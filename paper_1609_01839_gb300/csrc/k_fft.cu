@@ -59,13 +59,12 @@ __global__ void k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgSta
   if (do_sum) {
     // FP32 within a warp, FP64 across warps
     double* red = reinterpret_cast<double*>(smem + rpc * team_stride(L));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    part = warp_sum(part);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)part;
     __syncthreads();
     if (threadIdx.x == 0) {
       double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      for (int w = 0; w < num_warps(); ++w) s += red[w];
       atomicAdd(&st[cd.img0 + li].sum_u, s);
     }
   }
@@ -193,7 +192,7 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
 // the first evaluation of Eq. 11 at the nodes of the image's bracket.
 template <int M>
-__global__ void k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(256) k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs,
                                  ImgState* st, const float2* __restrict__ tw, int B,
                                  int iter) {
   extern __shared__ float2 smem[];
@@ -210,7 +209,7 @@ __global__ void k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs,
   const int col = c0 + b;
   float2* buf = smem + b * team_stride(M);
   float2* spec = d.S + col;
-  if (threadIdx.x < KNODES) s_nodes[threadIdx.x] = __ldcg(&S->node[threadIdx.x]);
+  for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int a = j + i * T;
@@ -279,7 +278,7 @@ __global__ void k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs,
 
 // Fallback evaluation of Eq. 11 over the stored spectrum U_E for images whose
 // root is still open; a block covers `chunk` packed elements of one image.
-__global__ void k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
+__global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                               int chunk, int iter, int last_chance) {
   __shared__ float s_nodes[KNODES];
   __shared__ double red[32 * (KNODES + 1)];
@@ -291,7 +290,7 @@ __global__ void k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, Im
   ImgState* S = st + gi;
   if (__ldcg(&S->need) == 0) return;
   const ImgDesc& d = imgs[gi];
-  if (threadIdx.x < KNODES) s_nodes[threadIdx.x] = __ldcg(&S->node[threadIdx.x]);
+  for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
   __syncthreads();
   float nodes[KNODES];
 #pragma unroll
@@ -361,7 +360,7 @@ GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool bra
 }
 
 template <int M>
-__global__ void k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(256) k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs,
                                 const ImgState* st, const float2* __restrict__ tw,
                                 const float* __restrict__ d2tab, int B) {
   extern __shared__ float2 smem[];
@@ -418,6 +417,18 @@ __global__ void k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs,
 // ---------------------------------------------------------------------------
 // launch configuration and dispatch
 // ---------------------------------------------------------------------------
+// Largest block the kernel can be launched with (registers permitting),
+// queried once per kernel.
+template <class K>
+static int max_threads(K kernel) {
+  static int cached = 0;
+  if (cached == 0) {
+    cudaFuncAttributes a{};
+    cached = cudaFuncGetAttributes(&a, (const void*)kernel) == cudaSuccess ? a.maxThreadsPerBlock : 256;
+  }
+  return cached;
+}
+
 static int rows_per_block(int L, int M) {
   const int T = threads_per_team(L);
   int r = 256 / T;
@@ -426,8 +437,9 @@ static int rows_per_block(int L, int M) {
   return r;
 }
 
-static int cols_per_block(int M, int Lc, int target_threads) {
+static int cols_per_block(int M, int Lc, int target_threads, int max_threads) {
   const int T = threads_per_team(M);
+  if (target_threads > max_threads) target_threads = max_threads;
   int B = target_threads / T;
   if (B < 1) B = 1;
   if (B > Lc) B = Lc;
@@ -503,7 +515,8 @@ template <int M>
 static void do_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst, bool inv,
                          cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 512);
+  const int B = cols_per_block(M, Lc, 512,
+                               inv ? max_threads(k_col_plain<M, true>) : max_threads(k_col_plain<M, false>));
   const size_t smem = (size_t)B * team_stride(M) * sizeof(float2);
   const int nblk = c.cd.n_img * (Lc / B);
   if (inv)
@@ -524,7 +537,7 @@ cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int
 template <int M>
 static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 512);
+  const int B = cols_per_block(M, Lc, 256, max_threads(k_col_fwd_lambda<M>));
   const int nthr = B * threads_per_team(M);
   const size_t smem = (size_t)B * team_stride(M) * sizeof(float2) +
                       (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
@@ -553,7 +566,7 @@ cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
 template <int M>
 static void do_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 256);
+  const int B = cols_per_block(M, Lc, 256, max_threads(k_col_solve_inv<M>));
   const size_t smem = (size_t)2 * B * team_stride(M) * sizeof(float2);
   const int nblk = c.cd.n_img * (Lc / B);
   k_col_solve_inv<M><<<nblk, B * threads_per_team(M), smem, s>>>(c.cd, c.imgs, c.st, t.tw,

@@ -62,20 +62,18 @@ GFD_D void accum_bin(float wr, float a, const float* nodes, float* acc) {
 // red must hold (blockDim/32) * (KNODES+1) doubles.  Ends synchronised.
 GFD_D void block_accumulate(float* acc, double* red, ImgState* st) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarp = blockDim.x >> 5;
+  const int nwarp = num_warps();
 #pragma unroll
   for (int j = 0; j <= KNODES; ++j) {
-    float v = acc[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const float v = warp_sum(acc[j]);
     if (lane == 0) red[warp * (KNODES + 1) + j] = (double)v;
   }
   __syncthreads();
-  if (threadIdx.x <= KNODES) {
+  for (int j = threadIdx.x; j <= KNODES; j += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < nwarp; ++w) s += red[w * (KNODES + 1) + threadIdx.x];
-    if (threadIdx.x < KNODES)
-      atomicAdd(&st->acc[threadIdx.x], s);
+    for (int w = 0; w < nwarp; ++w) s += red[w * (KNODES + 1) + j];
+    if (j < KNODES)
+      atomicAdd(&st->acc[j], s);
     else
       atomicAdd(&st->acc_res, s);
   }
