@@ -230,7 +230,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    probs = generate(shard_indices(rank, world))  # before any CUDA work
+    probs = generate(shard_indices(rank, world, args.images))  # before any CUDA work
     import paper_1609_01839_gb300 as gfd
 
     true_px = sum(p.true_shape[0] * p.true_shape[1] for p in probs)
@@ -390,6 +390,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-images", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--images", type=int, default=N_IMAGES,
+                    help="images per GPU (the workload is 256; smaller only for profiling)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the batched solves only (for profiler runs)")
     args = ap.parse_args(argv)
