@@ -418,10 +418,10 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   *out = nullptr;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
-  if (e != cudaSuccess) return GFD_ERR_CUDA;
+  if (e != cudaSuccess) return map_err(e);
   if (cuda_device < 0 || cuda_device >= ndev) return GFD_ERR_INVALID_ARG;
   if (opts && (opts->rho > 1.0 || !std::isfinite(opts->rho))) return GFD_ERR_INVALID_ARG;
-  if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return GFD_ERR_CUDA;
+  if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return map_err(e);
   gfdeconv_ctx* c = new (std::nothrow) gfdeconv_ctx();
   if (!c) return GFD_ERR_ALLOC;
   c->device = cuda_device;
@@ -435,7 +435,7 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   e = configure_kernels();
   if (e != cudaSuccess) {
     delete c;
-    return GFD_ERR_CUDA;
+    return map_err(e);
   }
   // twiddles W_4096^m and gradient weights 4 sin^2(pi m / 4096), in double, rounded once
   std::vector<float2> tw(TW_N);

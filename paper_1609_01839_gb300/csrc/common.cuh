@@ -54,6 +54,19 @@ GFD_D float warp_sum(float v) {
 }
 GFD_D int num_warps() { return (int)((blockDim.x + 31) >> 5); }
 
+// Asynchronous global -> shared copies (16-byte chunks, L2 only) with
+// commit groups; waits are hardware waits on the thread's own groups.
+GFD_D unsigned int smem_u32(const void* p) { return (unsigned int)__cvta_generic_to_shared(p); }
+GFD_D void cp_async16(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+               : "memory");
+}
+GFD_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+GFD_D void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Per-image solver state, one per image of a batch, in device memory.
 struct ImgState {
   double T;          // discrepancy target rho * P * sigma^2 (Sec. 3.2)

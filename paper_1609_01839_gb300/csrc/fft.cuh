@@ -120,9 +120,22 @@ GFD_D float2 twiddle(const float2* __restrict__ tw, int idx4096, bool inv) {
   return w;
 }
 
+// Shared-memory address of element a of a team's sequence.
+struct PaddedIdx {  // contiguous with one pad element per 16
+  GFD_D int operator()(int a) const { return phys(a); }
+};
+struct IdentIdx {  // contiguous, unpadded (landing buffers of rows)
+  GFD_D int operator()(int a) const { return a; }
+};
+struct StridedIdx {  // element a of column b of an interleaved [a][B] tile
+  int stride;
+  GFD_D int operator()(int a) const { return a * stride; }
+};
+
 template <int L, int R, bool INV, int s>
 struct Stage {
-  GFD_D static void run(float2* buf, int j, const float2* __restrict__ tw) {
+  template <class Idx>
+  GFD_D static void run(float2* buf, int j, const float2* __restrict__ tw, Idx idx) {
     constexpr int Ls = stage_len(L, R, s);
     if constexpr (Ls > 1) {
       constexpr int r = Ls < R ? Ls : R;
@@ -137,27 +150,71 @@ struct Stage {
         const int base = g * Ls + jj;
         float2 x[r];
 #pragma unroll
-        for (int i = 0; i < r; ++i) x[i] = buf[phys(base + i * Ln)];
+        for (int i = 0; i < r; ++i) x[i] = buf[idx(base + i * Ln)];
         DFT<r, INV>::run(x);
         if constexpr (Ln > 1) {
 #pragma unroll
           for (int i = 1; i < r; ++i) x[i] = cmul(x[i], twiddle(tw, jj * i * twstep, INV));
         }
 #pragma unroll
-        for (int i = 0; i < r; ++i) buf[phys(base + i * Ln)] = x[i];
+        for (int i = 0; i < r; ++i) buf[idx(base + i * Ln)] = x[i];
       }
       __syncthreads();
-      Stage<L, R, INV, s + 1>::run(buf, j, tw);
+      Stage<L, R, INV, s + 1>::run(buf, j, tw, idx);
     }
   }
 };
 
+// First stage reading from a separate (landing) buffer `in` addressed by
+// iidx, writing to buf addressed by idx; the remaining stages run in buf.
+template <int L, int R, bool INV>
+struct Stage0From {
+  template <class InIdx, class Idx>
+  GFD_D static void run(const float2* in, InIdx iidx, float2* buf, int j,
+                        const float2* __restrict__ tw, Idx idx) {
+    constexpr int Ls = L;
+    constexpr int r = Ls < R ? Ls : R;
+    constexpr int Ln = Ls / r;
+    constexpr int T = L / R;
+    constexpr int twstep = TW_N / Ls;
+#pragma unroll
+    for (int q = 0; q < R / r; ++q) {
+      const int beta = j + T * q;
+      const int g = beta / Ln;
+      const int jj = beta % Ln;
+      const int base = g * Ls + jj;
+      float2 x[r];
+#pragma unroll
+      for (int i = 0; i < r; ++i) x[i] = in[iidx(base + i * Ln)];
+      DFT<r, INV>::run(x);
+      if constexpr (Ln > 1) {
+#pragma unroll
+        for (int i = 1; i < r; ++i) x[i] = cmul(x[i], twiddle(tw, jj * i * twstep, INV));
+      }
+#pragma unroll
+      for (int i = 0; i < r; ++i) buf[idx(base + i * Ln)] = x[i];
+    }
+  }
+};
+
+// Transform whose input sits in `in` (read once, by the first stage) and
+// whose stages and output live in buf.  Ends block-synchronised, after which
+// `in` may be overwritten.
+template <int L, bool INV, class InIdx, class Idx = PaddedIdx>
+GFD_D void fft_team_from(const float2* in, InIdx iidx, float2* buf, int j,
+                         const float2* __restrict__ tw, Idx idx = Idx()) {
+  constexpr int R = radix_for(L);
+  Stage0From<L, R, INV>::run(in, iidx, buf, j, tw, idx);
+  __syncthreads();
+  Stage<L, R, INV, 1>::run(buf, j, tw, idx);
+}
+
 // Run the whole transform of one team (thread j of L/R) in place on buf.
 // Precondition: buf filled and a __syncthreads() issued by the caller.
-// Postcondition: X[k] at buf[phys(out_pos<L>(k))], block synchronised.
-template <int L, bool INV>
-GFD_D void fft_team(float2* buf, int j, const float2* __restrict__ tw) {
-  Stage<L, radix_for(L), INV, 0>::run(buf, j, tw);
+// Postcondition: X[k] at buf[idx(out_pos<L>(k))], block synchronised.
+template <int L, bool INV, class Idx = PaddedIdx>
+GFD_D void fft_team(float2* buf, int j, const float2* __restrict__ tw, Idx idx = Idx()) {
+  Stage<L, radix_for(L), INV, 0>::run(buf, j, tw, idx);
 }
 
 // position of output k after the in-place stages (digit reversal)

@@ -29,64 +29,88 @@ GFD_D float2* cplx_plane(const ImgDesc& d, int sel) {
 
 constexpr int threads_per_team(int L) { return L / radix_for(L); }
 
+// Persistent pass kernels.  Each block walks the work items item =
+// blockIdx.x + k * gridDim.x; the inputs of the next item are copied
+// asynchronously into a landing buffer while the current item's transform
+// runs in a separate (padded) work buffer, so that global loads stay in
+// flight while the block computes.
+
 // ---------------------------------------------------------------------------
-// Row pass, forward: real rows -> packed row spectra.
+// Row pass, forward: real rows -> packed row spectra.  An item is rpc
+// consecutive rows of one image (a contiguous block of memory).
 // Each row of N reals is read as N/2 complex z[n] = x[2n] + i x[2n+1];
 // Z = FFT_{N/2}(z); then X[k] = (Z[k] + conj Z[-k])/2 + W_N^k (Z[k] - conj Z[-k])/(2i)
 // and X[0], X[N/2] = Re Z[0] +- Im Z[0] (packed as X[0] + i X[N/2]).
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
-                          const float2* __restrict__ tw, int rpc, int src_sel, int dst_sel,
-                          int do_sum) {
-  extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs,
+                                                 ImgState* st, const float2* __restrict__ tw,
+                                                 int rpc, int src_sel, int dst_sel, int do_sum) {
+  extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(L), T = threads_per_team(L);
   constexpr int N = 2 * L;
+  const int item_elems = rpc * L;
+  float2* land = smem;
+  float2* work = smem + item_elems;
+  double* red = reinterpret_cast<double*>(work + rpc * team_stride(L));
   const int team = threadIdx.x / T, j = threadIdx.x % T;
-  const int row_c = blockIdx.x * rpc + team;  // row within the class
-  const int li = row_c / cd.M, row = row_c % cd.M;
-  const ImgDesc& d = imgs[cd.img0 + li];
-  float2* buf = smem + team * team_stride(L);
-  const float2* src = reinterpret_cast<const float2*>(real_plane(d, src_sel)) + (size_t)row * L;
-  float part = 0.0f;
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int n = j + i * T;
-    const float2 v = src[n];
-    buf[phys(n)] = v;
-    part += v.x + v.y;
-  }
-  if (do_sum) {
-    // FP32 within a warp, FP64 across warps
-    double* red = reinterpret_cast<double*>(smem + rpc * team_stride(L));
-    part = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)part;
+  const int n_items = cd.n_img * cd.M / rpc;
+  auto issue = [&](int item) {
+    if (item < n_items) {
+      const int row_c = item * rpc;
+      const ImgDesc& d = imgs[cd.img0 + row_c / cd.M];
+      const float2* src =
+          reinterpret_cast<const float2*>(real_plane(d, src_sel)) + (size_t)(row_c % cd.M) * L;
+      for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x)
+        cp_async16(land + 2 * c, src + 2 * c);
+    }
+    cp_async_commit();
+  };
+  issue(blockIdx.x);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    cp_async_wait<0>();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    const int row_c = item * rpc + team;
+    const int li = row_c / cd.M, row = row_c % cd.M;
+    const ImgDesc& d = imgs[cd.img0 + li];
+    float2* buf = work + team * team_stride(L);
+    const float2* in = land + team * L;
+    if (do_sum) {
+      float part = 0.0f;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const float2 v = in[j + i * T];
+        part += v.x + v.y;
+      }
+      part = warp_sum(part);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)part;
+    }
+    fft_team_from<L, false>(in, IdentIdx(), buf, j, tw);  // first stage reads land
+    issue(item + gridDim.x);                               // land is free again
+    if (do_sum && threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < num_warps(); ++w) s += red[w];
       atomicAdd(&st[cd.img0 + li].sum_u, s);
     }
-  }
-  __syncthreads();
-  fft_team<L, false>(buf, j, tw);
-  float2* dst = cplx_plane(d, dst_sel) + (size_t)row * L;
+    float2* dst = cplx_plane(d, dst_sel) + (size_t)row * L;
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int k = j + i * T;
-    const float2 Zk = buf[phys(out_pos<L>(k))];
-    float2 out;
-    if (k == 0) {
-      out = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
-    } else {
-      const float2 Zm = cconj(buf[phys(out_pos<L>(L - k))]);
-      const float2 E = cscale(cadd(Zk, Zm), 0.5f);
-      const float2 D = csub(Zk, Zm);
-      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
-      out = cadd(E, cmul(__ldg(&tw[k * (TW_N / N)]), O));
+    for (int i = 0; i < R; ++i) {
+      const int k = j + i * T;
+      const float2 Zk = buf[phys(out_pos<L>(k))];
+      float2 out;
+      if (k == 0) {
+        out = make_float2(Zk.x + Zk.y, Zk.x - Zk.y);
+      } else {
+        const float2 Zm = cconj(buf[phys(out_pos<L>(L - k))]);
+        const float2 E = cscale(cadd(Zk, Zm), 0.5f);
+        const float2 D = csub(Zk, Zm);
+        const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
+        out = cadd(E, cmul(__ldg(&tw[k * (TW_N / N)]), O));
+      }
+      dst[k] = out;
     }
-    dst[k] = out;
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -94,65 +118,88 @@ __global__ void k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgSta
 // Z[k] = (R[k] + conj R[L-k]) + i (R[k] - conj R[L-k]) W_N^{-k}, with
 // R[0], R[N/2] the real and imaginary parts of the packed entry 0; the
 // unnormalised inverse FFT of Z gives x[2n] + i x[2n+1] times N.
+// Items cover the rows of plane sel0, then of plane sel1 (if >= 0).
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs,
-                          const float2* __restrict__ tw, int rpc, int sel0, int sel1,
-                          float scale) {
-  extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(256, 3) k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs,
+                                                 const float2* __restrict__ tw, int rpc, int sel0,
+                                                 int sel1, float scale) {
+  extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(L), T = threads_per_team(L);
   constexpr int N = 2 * L;
+  const int item_elems = rpc * L;
+  float2* land = smem;
+  float2* work = smem + item_elems;
   const int team = threadIdx.x / T, j = threadIdx.x % T;
-  int blk = blockIdx.x;
-  int sel = sel0;
-  const int nblk_plane = cd.n_img * cd.M / rpc;
-  if (blk >= nblk_plane) {
-    blk -= nblk_plane;
-    sel = sel1;
-  }
-  const int row_c = blk * rpc + team;
-  const int li = row_c / cd.M, row = row_c % cd.M;
-  const ImgDesc& d = imgs[cd.img0 + li];
-  float2* buf = smem + team * team_stride(L);
-  float2* rowp = cplx_plane(d, sel) + (size_t)row * L;
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int n = j + i * T;
-    buf[phys(n)] = rowp[n];
-  }
-  __syncthreads();
-  for (int k = j; k <= L / 2; k += T) {
-    if (k == 0) {
-      const float2 t0 = buf[phys(0)];
-      buf[phys(0)] = make_float2(t0.x + t0.y, t0.x - t0.y);
-    } else {
-      const int km = L - k;
-      const float2 Rk = buf[phys(k)], Rm = buf[phys(km)];
-      {
-        const float2 E = cadd(Rk, cconj(Rm));
-        const float2 O = cmul(csub(Rk, cconj(Rm)), cconj(__ldg(&tw[k * (TW_N / N)])));
-        buf[phys(k)] = make_float2(E.x - O.y, E.y + O.x);
-      }
-      if (km != k) {
-        const float2 E = cadd(Rm, cconj(Rk));
-        const float2 O = cmul(csub(Rm, cconj(Rk)), cconj(__ldg(&tw[km * (TW_N / N)])));
-        buf[phys(km)] = make_float2(E.x - O.y, E.y + O.x);
+  const int per_plane = cd.n_img * cd.M / rpc;
+  const int n_items = sel1 >= 0 ? 2 * per_plane : per_plane;
+  auto rows_of = [&](int item, int& sel, int& row_c) {
+    sel = sel0;
+    if (item >= per_plane) {
+      item -= per_plane;
+      sel = sel1;
+    }
+    row_c = item * rpc;
+  };
+  auto issue = [&](int item) {
+    if (item < n_items) {
+      int sel, row_c;
+      rows_of(item, sel, row_c);
+      const ImgDesc& d = imgs[cd.img0 + row_c / cd.M];
+      const float2* src = cplx_plane(d, sel) + (size_t)(row_c % cd.M) * L;
+      for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x)
+        cp_async16(land + 2 * c, src + 2 * c);
+    }
+    cp_async_commit();
+  };
+  issue(blockIdx.x);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();
+    int sel, row_c0;
+    rows_of(item, sel, row_c0);
+    const int row_c = row_c0 + team;
+    const int li = row_c / cd.M, row = row_c % cd.M;
+    const ImgDesc& d = imgs[cd.img0 + li];
+    float2* buf = work + team * team_stride(L);
+    const float2* in = land + team * L;
+    for (int k = j; k <= L / 2; k += T) {
+      if (k == 0) {
+        const float2 t0 = in[0];
+        buf[phys(0)] = make_float2(t0.x + t0.y, t0.x - t0.y);
+      } else {
+        const int km = L - k;
+        const float2 Rk = in[k], Rm = in[km];
+        {
+          const float2 E = cadd(Rk, cconj(Rm));
+          const float2 O = cmul(csub(Rk, cconj(Rm)), cconj(__ldg(&tw[k * (TW_N / N)])));
+          buf[phys(k)] = make_float2(E.x - O.y, E.y + O.x);
+        }
+        if (km != k) {
+          const float2 E = cadd(Rm, cconj(Rk));
+          const float2 O = cmul(csub(Rm, cconj(Rk)), cconj(__ldg(&tw[km * (TW_N / N)])));
+          buf[phys(km)] = make_float2(E.x - O.y, E.y + O.x);
+        }
       }
     }
-  }
-  __syncthreads();
-  fft_team<L, true>(buf, j, tw);
+    __syncthreads();
+    issue(item + gridDim.x);
+    fft_team<L, true>(buf, j, tw);
+    float2* rowp = cplx_plane(d, sel) + (size_t)row * L;
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int n = j + i * T;
-    rowp[n] = cscale(buf[phys(out_pos<L>(n))], scale);
+    for (int i = 0; i < R; ++i) {
+      const int n = j + i * T;
+      rowp[n] = cscale(buf[phys(out_pos<L>(n))], scale);
+    }
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
-// Column passes.  A block owns B adjacent packed columns of one image; team b
-// (threads b, b+B, ...) transforms column c0+b, so that a warp's global
-// accesses cover B consecutive complex values of a row.
+// Column passes.  An item is B adjacent packed columns of one image; it lands
+// as an interleaved [M][B] tile (a warp's copies cover B consecutive complex
+// values of consecutive rows), and team b (threads b, b+B, ...) transforms
+// column c0+b.
 // ---------------------------------------------------------------------------
 template <int M, bool INV>
 __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
@@ -181,6 +228,15 @@ __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
   }
 }
 
+// copy B packed columns (rows 0..M-1) of plane p into an [M][B] tile
+GFD_D void issue_cols(float2* tile, const float2* plane, int M, int Lc, int B, int c0) {
+  const int per_row = B / 2;  // 16-byte chunks per row segment
+  for (int c = threadIdx.x; c < M * per_row; c += blockDim.x) {
+    const int a = c / per_row, q = c - a * per_row;
+    cp_async16(tile + a * B + 2 * q, plane + (size_t)a * Lc + c0 + 2 * q);
+  }
+}
+
 // unpack bins (k, 0) and (k, N/2) from packed column values S[k], S[-k]
 GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
   const float2 c = cconj(Smk);
@@ -192,88 +248,95 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
 // the first evaluation of Eq. 11 at the nodes of the image's bracket.
 template <int M>
-__global__ void __launch_bounds__(256) k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs,
-                                 ImgState* st, const float2* __restrict__ tw, int B,
-                                 int iter) {
-  extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
+k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
+                 const float2* __restrict__ tw, int B, int iter) {
+  extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
   __shared__ float s_nodes[KNODES];
   __shared__ int s_flag;
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
-  const int gi = cd.img0 + blockIdx.x / cpi;
-  const ImgDesc& d = imgs[gi];
-  ImgState* S = st + gi;
-  const int c0 = (blockIdx.x % cpi) * B;
+  const int n_items = cd.n_img * cpi;
+  float2* land = smem;
+  float2* work = smem + M * B;
+  double* red = reinterpret_cast<double*>(work + B * team_stride(M));
   const int b = threadIdx.x & (B - 1), j = threadIdx.x / B;
-  const int col = c0 + b;
-  float2* buf = smem + b * team_stride(M);
-  float2* spec = d.S + col;
-  for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
+  auto issue = [&](int item) {
+    if (item < n_items) issue_cols(land, imgs[cd.img0 + item / cpi].S, M, Lc, B, (item % cpi) * B);
+    cp_async_commit();
+  };
+  issue(blockIdx.x);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();
+    const int gi = cd.img0 + item / cpi;
+    const ImgDesc& d = imgs[gi];
+    ImgState* S = st + gi;
+    const int c0 = (item % cpi) * B;
+    const int col = c0 + b;
+    for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
+    float2* buf = work + b * team_stride(M);
+    fft_team_from<M, false>(land + b, StridedIdx{B}, buf, j, tw);
+    issue(item + gridDim.x);
+    float2* spec = d.S + col;
+    float nodes[KNODES];
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int a = j + i * T;
-    buf[phys(a)] = spec[(size_t)a * Lc];
-  }
-  __syncthreads();
-  fft_team<M, false>(buf, j, tw);
-  float nodes[KNODES];
+    for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
+    float acc[KNODES + 1];
 #pragma unroll
-  for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
-  float acc[KNODES + 1];
-#pragma unroll
-  for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
-  if (col != 0) {
-    const float2* Hc = d.H + col;
-    const float2* Yc = d.Y + col;
+    for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
+    if (col != 0) {
+      const float2* Hc = d.H + col;
+      const float2* Yc = d.Y + col;
 #pragma unroll 4
-    for (int i = 0; i < R; ++i) {
-      const int k = j + i * T;
-      const float2 U = buf[phys(out_pos<M>(k))];
-      spec[(size_t)k * Lc] = U;
-      const float2 H = __ldg(&Hc[(size_t)k * Lc]);
-      const float2 Y = __ldg(&Yc[(size_t)k * Lc]);
-      const float2 r = csub(cmul(H, U), Y);
-      const float rr = fmaf(r.x, r.x, r.y * r.y);
-      const float a = fmaf(H.x, H.x, H.y * H.y);
-      accum_bin(2.0f * rr, a, nodes, acc);  // bins l and N-l
-    }
-  } else {
-    for (int i = 0; i < R; ++i) {
-      const int k = j + i * T;
-      float2 U = buf[phys(out_pos<M>(k))];
-      const float2 Um = buf[phys(out_pos<M>((M - k) & (M - 1)))];
-      float2 UA, UB;
-      unpack_pair(U, Um, UA, UB);
-      const float2 HA = d.H0[k], HB = d.HN[k], YA = d.Y0[k], YB = d.YN[k];
-      float rA;
-      if (k == 0) {
-        // DC bin in FP64 from exact sums: d00 = sum(h) sum(u_E) - sum(y)
-        const double su = __ldcg(&S->sum_u);
-        const double d00 = S->sum_h * su - S->sum_y;
-        S->d00 = d00;
-        rA = (float)(d00 * d00);
-        U.x = (float)su;
-      } else {
-        const float2 r = csub(cmul(HA, UA), YA);
-        rA = fmaf(r.x, r.x, r.y * r.y);
+      for (int i = 0; i < R; ++i) {
+        const int k = j + i * T;
+        const float2 H = __ldg(&Hc[(size_t)k * Lc]);
+        const float2 Y = __ldg(&Yc[(size_t)k * Lc]);
+        const float2 U = buf[phys(out_pos<M>(k))];
+        spec[(size_t)k * Lc] = U;
+        const float2 r = csub(cmul(H, U), Y);
+        const float rr = fmaf(r.x, r.x, r.y * r.y);
+        const float a = fmaf(H.x, H.x, H.y * H.y);
+        accum_bin(2.0f * rr, a, nodes, acc);  // bins l and N-l
       }
-      const float2 rb = csub(cmul(HB, UB), YB);
-      accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
-      accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
-      spec[(size_t)k * Lc] = U;
+    } else {
+      for (int i = 0; i < R; ++i) {
+        const int k = j + i * T;
+        float2 U = buf[phys(out_pos<M>(k))];
+        const float2 Um = buf[phys(out_pos<M>((M - k) & (M - 1)))];
+        float2 UA, UB;
+        unpack_pair(U, Um, UA, UB);
+        const float2 HA = d.H0[k], HB = d.HN[k], YA = d.Y0[k], YB = d.YN[k];
+        float rA;
+        if (k == 0) {
+          // DC bin in FP64 from exact sums: d00 = sum(h) sum(u_E) - sum(y)
+          const double su = __ldcg(&S->sum_u);
+          const double d00 = S->sum_h * su - S->sum_y;
+          S->d00 = d00;
+          rA = (float)(d00 * d00);
+          U.x = (float)su;
+        } else {
+          const float2 r = csub(cmul(HA, UA), YA);
+          rA = fmaf(r.x, r.x, r.y * r.y);
+        }
+        const float2 rb = csub(cmul(HB, UB), YB);
+        accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
+        accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
+        spec[(size_t)k * Lc] = U;
+      }
+    }
+    block_accumulate(acc, red, S);
+    if (last_block(&S->cta_done, cpi, &s_flag)) {
+      if (threadIdx.x == 0) {
+        lambda_update(S, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out);
+        S->cta_done = 0;
+        __threadfence();
+      }
     }
   }
-  double* red = reinterpret_cast<double*>(smem + B * team_stride(M));
-  __syncthreads();
-  block_accumulate(acc, red, S);
-  if (last_block(&S->cta_done, cpi, &s_flag)) {
-    if (threadIdx.x == 0) {
-      lambda_update(S, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out);
-      S->cta_done = 0;
-      __threadfence();
-    }
-  }
+  cp_async_wait<0>();
 }
 
 // Fallback evaluation of Eq. 11 over the stored spectrum U_E for images whose
@@ -359,66 +422,104 @@ GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool bra
   }
 }
 
+// Spectral solves fused with the inverse column FFTs: an item's U_E, H and Y
+// columns land together (U_E only for M = 4096, where three landing tiles
+// would not fit beside the work tiles; H and Y are then read directly);
+// Eq. 8 and 9 fill two work tiles (U_I, U_p) that are inverse-transformed
+// while the next item's columns are fetched.
 template <int M>
-__global__ void __launch_bounds__(256) k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs,
-                                const ImgState* st, const float2* __restrict__ tw,
-                                const float* __restrict__ d2tab, int B) {
-  extern __shared__ float2 smem[];
+__global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
+k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st,
+                const float2* __restrict__ tw, const float* __restrict__ d2tab, int B) {
+  extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
   const int N = cd.N, Lc = N / 2;
   const int cpi = Lc / B;
-  const int gi = cd.img0 + blockIdx.x / cpi;
-  const ImgDesc& d = imgs[gi];
-  const int c0 = (blockIdx.x % cpi) * B;
+  const int n_items = cd.n_img * cpi;
+  constexpr bool HY_LAND = M < 4096;
+  float2* landU = smem;
+  float2* landH = landU + M * B;
+  float2* landY = landH + M * B;
+  float2* workI = HY_LAND ? landY + M * B : landH;
+  float2* workP = workI + B * team_stride(M);
   const int b = threadIdx.x & (B - 1), j = threadIdx.x / B;
-  const int col = c0 + b;
-  float2* bufI = smem + b * team_stride(M);
-  float2* bufP = smem + (B + b) * team_stride(M);
-  const double lamd = __ldcg(&st[gi].lam);
-  const bool branch = !(lamd < 1e300);
-  const float lam = branch ? 0.0f : (float)lamd;
-  const int nstep = TW_N / N;  // d2tab stride for the column frequency
-  const float d2c = __ldg(&d2tab[col * nstep]);
-#pragma unroll 4
-  for (int i = 0; i < R; ++i) {
-    const int k = j + i * T;
-    const size_t e = (size_t)k * Lc + col;
-    const float d2r = __ldg(&d2tab[k * (TW_N / M)]);
-    const float2 U = d.S[e];
-    float2 UI, Up;
-    if (col != 0) {
-      solve_bin(U, __ldg(&d.H[e]), __ldg(&d.Y[e]), lam, d2r + d2c, branch, UI, Up);
-    } else {
-      const float2 Um = d.S[(size_t)((M - k) & (M - 1)) * Lc];
-      float2 UA, UB, IA, IB, PA, PB;
-      unpack_pair(U, Um, UA, UB);
-      solve_bin(UA, d.H0[k], d.Y0[k], lam, d2r, branch, IA, PA);
-      solve_bin(UB, d.HN[k], d.YN[k], lam, d2r + 4.0f, branch, IB, PB);
-      UI = make_float2(IA.x - IB.y, IA.y + IB.x);  // A + i B
-      Up = make_float2(PA.x - PB.y, PA.y + PB.x);
+  auto issue = [&](int item) {
+    if (item < n_items) {
+      const ImgDesc& d = imgs[cd.img0 + item / cpi];
+      const int c0 = (item % cpi) * B;
+      issue_cols(landU, d.S, M, Lc, B, c0);
+      if constexpr (HY_LAND) {
+        issue_cols(landH, d.H, M, Lc, B, c0);
+        issue_cols(landY, d.Y, M, Lc, B, c0);
+      }
     }
-    bufI[phys(k)] = UI;
-    bufP[phys(k)] = Up;
-  }
-  __syncthreads();
-  fft_team<M, true>(bufI, j, tw);
-  fft_team<M, true>(bufP, j, tw);
-  float2* qi = d.QI + col;
-  float2* qp = d.Qp + col;
+    cp_async_commit();
+  };
+  issue(blockIdx.x);
+  const int nstep = TW_N / N;  // d2tab stride for the column frequency
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();
+    const int gi = cd.img0 + item / cpi;
+    const ImgDesc& d = imgs[gi];
+    const int c0 = (item % cpi) * B;
+    const int col = c0 + b;
+    const double lamd = __ldcg(&st[gi].lam);
+    const bool branch = !(lamd < 1e300);
+    const float lam = branch ? 0.0f : (float)lamd;
+    const float d2c = __ldg(&d2tab[col * nstep]);
+    float2* bufI = workI + b * team_stride(M);
+    float2* bufP = workP + b * team_stride(M);
+#pragma unroll 4
+    for (int i = 0; i < R; ++i) {
+      const int k = j + i * T;
+      const int e = k * B + b;
+      const float d2r = __ldg(&d2tab[k * (TW_N / M)]);
+      const float2 U = landU[e];
+      float2 UI, Up;
+      if (col != 0) {
+        float2 Hv, Yv;
+        if constexpr (HY_LAND) {
+          Hv = landH[e];
+          Yv = landY[e];
+        } else {
+          Hv = __ldg(&d.H[(size_t)k * Lc + col]);
+          Yv = __ldg(&d.Y[(size_t)k * Lc + col]);
+        }
+        solve_bin(U, Hv, Yv, lam, d2r + d2c, branch, UI, Up);
+      } else {
+        const float2 Um = landU[((M - k) & (M - 1)) * B + b];
+        float2 UA, UB, IA, IB, PA, PB;
+        unpack_pair(U, Um, UA, UB);
+        solve_bin(UA, d.H0[k], d.Y0[k], lam, d2r, branch, IA, PA);
+        solve_bin(UB, d.HN[k], d.YN[k], lam, d2r + 4.0f, branch, IB, PB);
+        UI = make_float2(IA.x - IB.y, IA.y + IB.x);  // A + i B
+        Up = make_float2(PA.x - PB.y, PA.y + PB.x);
+      }
+      bufI[phys(k)] = UI;
+      bufP[phys(k)] = Up;
+    }
+    __syncthreads();
+    issue(item + gridDim.x);
+    fft_team<M, true>(bufI, j, tw);
+    fft_team<M, true>(bufP, j, tw);
+    float2* qi = d.QI + col;
+    float2* qp = d.Qp + col;
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int k = j + i * T;
-    const int p = phys(out_pos<M>(k));
-    qi[(size_t)k * Lc] = bufI[p];
-    qp[(size_t)k * Lc] = bufP[p];
+    for (int i = 0; i < R; ++i) {
+      const int k = j + i * T;
+      const int p = phys(out_pos<M>(k));
+      qi[(size_t)k * Lc] = bufI[p];
+      qp[(size_t)k * Lc] = bufP[p];
+    }
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
 // launch configuration and dispatch
 // ---------------------------------------------------------------------------
-// Largest block the kernel can be launched with (registers permitting),
-// queried once per kernel.
+// Largest block the kernel can be launched with (registers permitting).
 template <class K>
 static int max_threads(K kernel) {
   static int cached = 0;
@@ -429,25 +530,50 @@ static int max_threads(K kernel) {
   return cached;
 }
 
-static int rows_per_block(int L, int M) {
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Persistent grid: as many blocks as fit on the device at once (never more
+// than there are items).
+template <class K>
+static int persistent_grid(K kernel, int threads, size_t smem, int n_items) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long g = (long long)per_sm * sm_count();
+  return (int)(g < n_items ? g : n_items);
+}
+
+TileConfig g_tiles;
+
+static int rows_per_item(int L, int M) {
   const int T = threads_per_team(L);
-  int r = 256 / T;
+  int r = g_tiles.row_threads / T;
   if (r < 1) r = 1;
   if (r > M) r = M;
   return r;
 }
 
-static int cols_per_block(int M, int Lc, int target_threads, int max_threads) {
+static int cols_per_item(int M, int Lc, int threads, int max_thr) {
   const int T = threads_per_team(M);
-  if (target_threads > max_threads) target_threads = max_threads;
-  int B = target_threads / T;
-  if (B < 1) B = 1;
+  if (threads > max_thr) threads = max_thr;
+  int B = threads / T;
+  if (B < 2) B = 2;  // 16-byte copy chunks hold two columns
   if (B > Lc) B = Lc;
   return B;
 }
 
 static size_t row_smem(int L, int rpc) {
-  return (size_t)rpc * team_stride(L) * sizeof(float2) + 32 * sizeof(double);
+  return (size_t)rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
+         32 * sizeof(double);
 }
 
 #define GFD_CASE_L(F, ...)             \
@@ -477,10 +603,12 @@ static size_t row_smem(int L, int rpc) {
 template <int L>
 static void do_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst, int sum,
                        cudaStream_t s) {
-  const int rpc = rows_per_block(L, c.cd.M);
-  const int nblk = c.cd.n_img * c.cd.M / rpc;
-  k_row_r2c<L><<<nblk, rpc * threads_per_team(L), row_smem(L, rpc), s>>>(
-      c.cd, c.imgs, c.st, t.tw, rpc, src, dst, sum);
+  const int rpc = rows_per_item(L, c.cd.M);
+  const int n_items = c.cd.n_img * c.cd.M / rpc;
+  const int thr = rpc * threads_per_team(L);
+  const size_t smem = row_smem(L, rpc);
+  const int grid = persistent_grid(k_row_r2c<L>, thr, smem, n_items);
+  k_row_r2c<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, rpc, src, dst, sum);
 }
 
 cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst,
@@ -495,11 +623,13 @@ cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int d
 template <int L>
 static void do_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, float scale,
                        cudaStream_t s) {
-  const int rpc = rows_per_block(L, c.cd.M);
-  int nblk = c.cd.n_img * c.cd.M / rpc;
-  if (sel1 >= 0) nblk *= 2;
-  k_row_c2r<L><<<nblk, rpc * threads_per_team(L), row_smem(L, rpc), s>>>(
-      c.cd, c.imgs, t.tw, rpc, sel0, sel1, scale);
+  const int rpc = rows_per_item(L, c.cd.M);
+  int n_items = c.cd.n_img * c.cd.M / rpc;
+  if (sel1 >= 0) n_items *= 2;
+  const int thr = rpc * threads_per_team(L);
+  const size_t smem = row_smem(L, rpc);
+  const int grid = persistent_grid(k_row_c2r<L>, thr, smem, n_items);
+  k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, scale);
 }
 
 cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1,
@@ -515,8 +645,11 @@ template <int M>
 static void do_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst, bool inv,
                          cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 512,
-                               inv ? max_threads(k_col_plain<M, true>) : max_threads(k_col_plain<M, false>));
+  int B = 512 / threads_per_team(M);
+  const int mt = inv ? max_threads(k_col_plain<M, true>) : max_threads(k_col_plain<M, false>);
+  if (B * threads_per_team(M) > mt) B = mt / threads_per_team(M);
+  if (B < 1) B = 1;
+  if (B > Lc) B = Lc;
   const size_t smem = (size_t)B * team_stride(M) * sizeof(float2);
   const int nblk = c.cd.n_img * (Lc / B);
   if (inv)
@@ -537,12 +670,14 @@ cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int
 template <int M>
 static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 256, max_threads(k_col_fwd_lambda<M>));
+  const int B = cols_per_item(M, Lc, M >= 4096 ? 512 : g_tiles.col_threads,
+                              max_threads(k_col_fwd_lambda<M>));
   const int nthr = B * threads_per_team(M);
-  const size_t smem = (size_t)B * team_stride(M) * sizeof(float2) +
+  const size_t smem = (size_t)M * B * sizeof(float2) + (size_t)B * team_stride(M) * sizeof(float2) +
                       (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
-  const int nblk = c.cd.n_img * (Lc / B);
-  k_col_fwd_lambda<M><<<nblk, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, B, iter);
+  const int n_items = c.cd.n_img * (Lc / B);
+  const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items);
+  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, B, iter);
 }
 
 cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter,
@@ -566,11 +701,14 @@ cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
 template <int M>
 static void do_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  const int B = cols_per_block(M, Lc, 256, max_threads(k_col_solve_inv<M>));
-  const size_t smem = (size_t)2 * B * team_stride(M) * sizeof(float2);
-  const int nblk = c.cd.n_img * (Lc / B);
-  k_col_solve_inv<M><<<nblk, B * threads_per_team(M), smem, s>>>(c.cd, c.imgs, c.st, t.tw,
-                                                                   t.d2, B);
+  const int B = cols_per_item(M, Lc, M >= 4096 ? 512 : g_tiles.solve_threads,
+                              max_threads(k_col_solve_inv<M>));
+  const int nthr = B * threads_per_team(M);
+  const size_t smem = (size_t)(M < 4096 ? 3 : 1) * M * B * sizeof(float2) +
+                      (size_t)2 * B * team_stride(M) * sizeof(float2);
+  const int n_items = c.cd.n_img * (Lc / B);
+  const int grid = persistent_grid(k_col_solve_inv<M>, nthr, smem, n_items);
+  k_col_solve_inv<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, t.d2, B);
 }
 
 cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {
@@ -582,19 +720,30 @@ cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStre
 }
 
 // ---------------------------------------------------------------------------
+static int smem_optin() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+      v = 48 * 1024;
+  }
+  return v;
+}
+
 template <int L>
 static cudaError_t cfg_row() {
-  cudaError_t e = cudaFuncSetAttribute(k_row_r2c<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_row_r2c<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_row_c2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(k_row_c2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
 }
 template <int M>
 static cudaError_t cfg_col() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_col_plain<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_col_plain<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_col_fwd_lambda<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_col_solve_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if ((e = cudaFuncSetAttribute(k_col_plain<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_col_plain<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_col_fwd_lambda<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_col_solve_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
 }
 
 cudaError_t configure_fft_kernels() {

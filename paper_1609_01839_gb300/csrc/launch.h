@@ -16,6 +16,15 @@ enum PlaneSel : int {
   SEL_YS = 6,  // observation spectrum
 };
 
+// Tile shapes of the pass kernels (threads per block, which fixes rows per
+// row item and columns per column item); set by the autotuner.
+struct TileConfig {
+  int row_threads = 256;
+  int col_threads = 256;
+  int solve_threads = 256;
+};
+extern TileConfig g_tiles;
+
 struct Tables {
   const float2* tw;   // W_4096^m
   const float* d2;    // 4 sin^2(pi m / 4096)
