@@ -731,19 +731,29 @@ static int smem_optin() {
   return v;
 }
 
+// Allow the kernel the device's opt-in shared memory minus its static part.
+template <class K>
+static cudaError_t allow_smem(K kernel) {
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, (const void*)kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_optin() - (int)a.sharedSizeBytes);
+}
+
 template <int L>
 static cudaError_t cfg_row() {
-  cudaError_t e = cudaFuncSetAttribute(k_row_r2c<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+  cudaError_t e = allow_smem(k_row_r2c<L>);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_row_c2r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+  return allow_smem(k_row_c2r<L>);
 }
 template <int M>
 static cudaError_t cfg_col() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_col_plain<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_col_plain<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_col_fwd_lambda<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin())) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_col_solve_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+  if ((e = allow_smem(k_col_plain<M, false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_col_plain<M, true>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_col_fwd_lambda<M>)) != cudaSuccess) return e;
+  return allow_smem(k_col_solve_inv<M>);
 }
 
 cudaError_t configure_fft_kernels() {

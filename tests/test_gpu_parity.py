@@ -287,7 +287,8 @@ def test_lambda_infinite_branch(ctx):
     assert np.abs(host(u) - ref["u"]).max() < 1e-7
 
 
-@pytest.mark.parametrize("M,N,w,k", [(8, 8, 9, 3), (8, 16, 3, 5), (16, 64, 5, 9), (128, 32, 7, 15)])
+@pytest.mark.parametrize("M,N,w,k", [(8, 8, 9, 3), (8, 16, 3, 5), (16, 64, 5, 9), (128, 32, 7, 15),
+                                     (4096, 64, 5, 9), (64, 4096, 9, 15), (2048, 128, 3, 5)])
 def test_small_and_nonsquare(ctx, M, N, w, k):
     rng = np.random.default_rng(M * N + w)
     u0 = S.image_polygons(11, M, N, n_poly=3, texture_std=0.02, rng=rng)
