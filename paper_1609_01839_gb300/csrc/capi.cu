@@ -115,9 +115,19 @@ int validate_image(const gfdeconv_image& im, int iters) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// per-item partial sums of the spectral passes: column items hold >= 2
+// columns, fallback-pass items >= 4096 bins (or the whole image)
+size_t part_doubles(int M, int N) {
+  const size_t Lc = (size_t)N / 2;
+  const size_t col_items = Lc / 2;
+  const size_t pass_items = (size_t)M * Lc / 4096 + 1;
+  return (KNODES + 1) * (col_items > pass_items ? col_items : pass_items);
+}
+
 size_t image_ws_bytes(int M, int N) {
   const size_t P = (size_t)M * N;
-  return 5 * align256(P * sizeof(float)) + 4 * align256((size_t)M * sizeof(float2));
+  return 5 * align256(P * sizeof(float)) + 4 * align256((size_t)M * sizeof(float2)) +
+         align256(part_doubles(M, N) * sizeof(double)) + align256((size_t)M * sizeof(double));
 }
 
 cudaError_t ensure_ws(gfdeconv_ctx* c, size_t bytes) {
@@ -232,6 +242,10 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
         *pp = reinterpret_cast<float2*>(cur);
         cur += align256((size_t)im.M * sizeof(float2));
       }
+      d.part = reinterpret_cast<double*>(cur);
+      cur += align256(part_doubles(im.M, im.N) * sizeof(double));
+      d.rowsum = reinterpret_cast<double*>(cur);
+      cur += align256((size_t)im.M * sizeof(double));
       cl.max_rad = std::max(cl.max_rad, (im.w - 1) / 2);
       pl.order.push_back(ui);
       pl.h_imgs.push_back(d);

@@ -80,13 +80,11 @@ struct ImgState {
   double lo, hi;     // bracket of the nodes of the next pass
   double lam_up;     // upper bound of the root from res and amax
   double res;        // ||h*u_E - y||^2 of the current iteration
-  double acc[KNODES];// FP64 accumulators of sum w r t_j^2 at the nodes
-  double acc_res;    // FP64 accumulator of sum w r
   double sum_u;      // FP64 sum of the current iterate u_E (its DC bin)
   double d00;        // DC residual sum(h) sum(u_E) - sum(y), FP64
   double err2;       // FP64 sum (u - u_orig)^2
   float node[KNODES];// node values lambda_j (float) of the pending pass
-  unsigned int cta_done;   // last-block-done counter (spectral passes)
+  unsigned int cta_done;   // items of the current spectral pass completed
   unsigned int gf_done;    // last-block-done counter (guided filter)
   int need;          // 1: lambda unresolved, a fallback pass must run
   int status;        // ST_* bits
@@ -115,6 +113,8 @@ struct ImgDesc {
   float2* HN;         // H(k, N/2)
   float2* Y0;         // Y(k, 0)
   float2* YN;         // Y(k, N/2)
+  double* part;       // per-item partial sums of a spectral pass, (KNODES+1) each
+  double* rowsum;     // per-item sums of the iterate from the forward row pass
 };
 
 // One size class of a batch: all images with the same canvas M x N.

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc*
     if (do_sum && threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < num_warps(); ++w) s += red[w];
-      atomicAdd(&st[cd.img0 + li].sum_u, s);
+      d.rowsum[row / rpc] = s;  // one partial per item, summed by the column pass
     }
     float2* dst = cplx_plane(d, dst_sel) + (size_t)row * L;
 #pragma unroll
@@ -250,10 +250,11 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
-                 const float2* __restrict__ tw, int B, int iter) {
+                 const float2* __restrict__ tw, int B, int iter, int row_items) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
   __shared__ float s_nodes[KNODES];
+  __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
@@ -279,6 +280,10 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     float2* buf = work + b * team_stride(M);
     fft_team_from<M, false>(land + b, StridedIdx{B}, buf, j, tw);
     issue(item + gridDim.x);
+    if (c0 == 0) {  // the DC bin needs sum(u_E): total of the row pass's partials
+      block_sum_columns(d.rowsum, row_items, 1, 1, red, s_tot);
+      if (threadIdx.x == 0) S->sum_u = s_tot[0];
+    }
     float2* spec = d.S + col;
     float nodes[KNODES];
 #pragma unroll
@@ -312,7 +317,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         float rA;
         if (k == 0) {
           // DC bin in FP64 from exact sums: d00 = sum(h) sum(u_E) - sum(y)
-          const double su = __ldcg(&S->sum_u);
+          const double su = s_tot[0];
           const double d00 = S->sum_h * su - S->sum_y;
           S->d00 = d00;
           rA = (float)(d00 * d00);
@@ -327,10 +332,11 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         spec[(size_t)k * Lc] = U;
       }
     }
-    block_accumulate(acc, red, S);
-    if (last_block(&S->cta_done, cpi, &s_flag)) {
+    block_partials(acc, red, d.part + (size_t)(item % cpi) * (KNODES + 1));
+    if (last_item(&S->cta_done, cpi, &s_flag)) {
+      block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
       if (threadIdx.x == 0) {
-        lambda_update(S, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out);
+        lambda_update(S, s_tot, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out);
         S->cta_done = 0;
         __threadfence();
       }
@@ -345,6 +351,7 @@ __global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc
                               int chunk, int iter, int last_chance) {
   __shared__ float s_nodes[KNODES];
   __shared__ double red[32 * (KNODES + 1)];
+  __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
   const int Lc = cd.N / 2;
   const int per_img = cd.M * Lc;
@@ -388,10 +395,12 @@ __global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc
       accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
     }
   }
-  block_accumulate(acc, red, S);
-  if (last_block(&S->cta_done, cpi, &s_flag)) {
+  block_partials(acc, red, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
+  if (last_item(&S->cta_done, cpi, &s_flag)) {
+    block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
     if (threadIdx.x == 0) {
-      lambda_update(S, (double)cd.M * cd.N, false, last_chance != 0, iter, d.lam_out, d.res_out);
+      lambda_update(S, s_tot, (double)cd.M * cd.N, false, last_chance != 0, iter, d.lam_out,
+                    d.res_out);
       S->cta_done = 0;
       __threadfence();
     }
@@ -677,7 +686,8 @@ static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, c
                       (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items);
-  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, B, iter);
+  const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M);
+  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, B, iter, row_items);
 }
 
 cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter,

@@ -57,10 +57,10 @@ GFD_D void accum_bin(float wr, float a, const float* nodes, float* acc) {
   }
 }
 
-// Block-wide sum of the KNODES+1 per-thread partials (FP32 within a warp,
-// FP64 across warps), added atomically to the image's accumulators.
-// red must hold (blockDim/32) * (KNODES+1) doubles.  Ends synchronised.
-GFD_D void block_accumulate(float* acc, double* red, ImgState* st) {
+// Block-wide sums of the KNODES+1 per-thread partials (FP32 within a warp,
+// FP64 across warps), stored with plain stores to part[0..KNODES].
+// red must hold num_warps() * (KNODES+1) doubles.  Ends synchronised.
+GFD_D void block_partials(float* acc, double* red, double* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarp = num_warps();
 #pragma unroll
@@ -72,13 +72,56 @@ GFD_D void block_accumulate(float* acc, double* red, ImgState* st) {
   for (int j = threadIdx.x; j <= KNODES; j += blockDim.x) {
     double s = 0.0;
     for (int w = 0; w < nwarp; ++w) s += red[w * (KNODES + 1) + j];
-    if (j < KNODES)
-      atomicAdd(&st->acc[j], s);
-    else
-      atomicAdd(&st->acc_res, s);
+    part[j] = s;
   }
+  __syncthreads();
+}
+
+GFD_D double warp_sum_dbl(double v) {
+  const unsigned int n = blockDim.x < 32 ? blockDim.x : 32u;
+  const unsigned int mask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    if ((unsigned)o < n) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// Sum of vals[i * stride + j] over i < n for each j < m, by the whole block
+// in FP64 (loads bypass L1: the values were written by other blocks).
+// Results land in sums[0..m) (shared), visible to every thread on return.
+GFD_D void block_sum_columns(const double* vals, int n, int stride, int m, double* red,
+                             double* sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = num_warps();
+  for (int j = 0; j < m; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(&vals[(size_t)i * stride + j]);
+    s = warp_sum_dbl(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarp; ++w) t += red[w];
+      sums[j] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Called by every block after storing its item's partials: true in exactly
+// one block per image and pass (the one finishing last), after all partials
+// are visible.
+GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
   __threadfence();
   __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *s_flag = (prev == n_items - 1);
+  }
+  __syncthreads();
+  const bool last = *s_flag != 0;
+  if (last) __threadfence();
+  return last;
 }
 
 // Barycentric interpolant of (s_m, f_m) at s.
@@ -139,24 +182,17 @@ GFD_D void resolve(ImgState* st, double lam, int iter, double* lam_out) {
   if (isfinite(lam) && lam > 0.0) set_bracket(st, lam / PRIMARY_RATIO, lam * PRIMARY_RATIO);
 }
 
-GFD_D double ld(const double* p) { return __ldcg(p); }
-
 // Consume the accumulators of the pass that just completed for this image.
 // Run by one thread of the image's last block.
-GFD_D void lambda_update(ImgState* st, double P, bool primary, bool last_chance, int iter,
-                         double* lam_out, double* res_out) {
+GFD_D void lambda_update(ImgState* st, const double* tot, double P, bool primary,
+                         bool last_chance, int iter, double* lam_out, double* res_out) {
   double f[KNODES];
-  for (int j = 0; j < KNODES; ++j) {
-    f[j] = ld(&st->acc[j]) / P;
-    st->acc[j] = 0.0;
-  }
-  const double resinf = ld(&st->acc_res) / P;
-  st->acc_res = 0.0;
+  for (int j = 0; j < KNODES; ++j) f[j] = tot[j] / P;
+  const double resinf = tot[KNODES] / P;
   const double T = st->T;
   if (primary) {
     st->res = resinf;
     if (res_out) res_out[iter] = resinf;
-    st->sum_u = 0.0;
     if (!isfinite(resinf)) {
       st->status |= ST_NONFINITE;
       resolve(st, INFINITY, iter, lam_out);
@@ -208,19 +244,6 @@ GFD_D void lambda_update(ImgState* st, double P, bool primary, bool last_chance,
       resolve(st, sqrt(st->lo * st->hi), iter, lam_out);
     }
   }
-}
-
-// Last-block-done bookkeeping: returns true in exactly one block per image
-// and pass, after every block's atomics are visible.
-GFD_D bool last_block(unsigned int* counter, unsigned int nblocks, int* s_flag) {
-  if (threadIdx.x == 0) {
-    const unsigned int prev = atomicAdd(counter, 1u);
-    *s_flag = (prev == nblocks - 1);
-  }
-  __syncthreads();
-  const bool last = *s_flag != 0;
-  if (last) __threadfence();
-  return last;
 }
 
 }  // namespace gfd
