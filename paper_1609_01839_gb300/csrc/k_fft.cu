@@ -335,8 +335,10 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     block_partials(acc, red, d.part + (size_t)(item % cpi) * (KNODES + 1));
     if (last_item(&S->cta_done, cpi, &s_flag)) {
       block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
+      if (threadIdx.x < 32)
+        lambda_update_warp(S, s_tot, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out,
+                           threadIdx.x);
       if (threadIdx.x == 0) {
-        lambda_update(S, s_tot, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out);
         S->cta_done = 0;
         __threadfence();
       }
@@ -398,9 +400,10 @@ __global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc
   block_partials(acc, red, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
   if (last_item(&S->cta_done, cpi, &s_flag)) {
     block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
+    if (threadIdx.x < 32)
+      lambda_update_warp(S, s_tot, (double)cd.M * cd.N, false, last_chance != 0, iter,
+                         d.lam_out, d.res_out, threadIdx.x);
     if (threadIdx.x == 0) {
-      lambda_update(S, s_tot, (double)cd.M * cd.N, false, last_chance != 0, iter, d.lam_out,
-                    d.res_out);
       S->cta_done = 0;
       __threadfence();
     }

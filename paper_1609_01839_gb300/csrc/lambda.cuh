@@ -35,15 +35,45 @@ constexpr double EST_HALF_WIDTH = 0.02;
 constexpr double PRIMARY_RATIO = 2.0;
 constexpr double INITIAL_LO = 1e-10, INITIAL_HI = 1e10;
 
+// cos(pi j / (KNODES - 1)), j = 0..KNODES-1 (Chebyshev-Lobatto points)
+__device__ constexpr double kLobatto[KNODES] = {
+    1.0, 0.9594929736144974, 0.8412535328311812, 0.6548607339452851,
+    0.41541501300188644, 0.14231483827328512, -0.142314838273285, -0.4154150130018863,
+    -0.654860733945285, -0.8412535328311811, -0.9594929736144974, -1.0};
+
+// Nodes of the next pass over [lo, hi], computed by the lanes of one warp
+// (lane j < KNODES owns node j).  The per-bin arithmetic uses the node
+// rounded to float; its exact logarithm (s + log1p(e), e the rounding's
+// relative error) is kept as the interpolation abscissa.
+GFD_D void set_bracket_warp(ImgState* st, double lo, double hi, int lane) {
+  if (lane == 0) {
+    st->lo = lo;
+    st->hi = hi;
+  }
+  if (lane < KNODES) {
+    const double a = log(lo), b = log(hi);
+    const double sj = 0.5 * (a + b) - 0.5 * (b - a) * kLobatto[lane];
+    const double e = exp(sj);
+    const float lf = (float)e;
+    const double rel = (double)lf / e - 1.0;
+    st->node[lane] = lf;
+    st->snode[lane] = sj + rel - 0.5 * rel * rel;
+  }
+  __syncwarp();
+}
+
+// Single-thread variant for the setup kernel.
 GFD_D void set_bracket(ImgState* st, double lo, double hi) {
   st->lo = lo;
   st->hi = hi;
   const double a = log(lo), b = log(hi);
-  const double c = 0.5 * (a + b), h = 0.5 * (b - a);
-#pragma unroll
   for (int j = 0; j < KNODES; ++j) {
-    const double s = c - h * cos(PI_D * j / (KNODES - 1));
-    st->node[j] = (float)exp(s);
+    const double sj = 0.5 * (a + b) - 0.5 * (b - a) * kLobatto[j];
+    const double e = exp(sj);
+    const float lf = (float)e;
+    const double rel = (double)lf / e - 1.0;
+    st->node[j] = lf;
+    st->snode[j] = sj + rel - 0.5 * rel * rel;
   }
 }
 
@@ -124,124 +154,144 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
   return last;
 }
 
-// Barycentric interpolant of (s_m, f_m) at s.
-GFD_D double bary_eval(const double* s, const double* f, const double* wb, double x) {
-  double num = 0.0, den = 0.0;
+GFD_D double warp_sum_full(double v) {
 #pragma unroll
-  for (int m = 0; m < KNODES; ++m) {
-    const double d = x - s[m];
-    if (d == 0.0) return f[m];
-    const double t = wb[m] / d;
-    num += t * f[m];
-    den += t;
-  }
-  return num / den;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// Root of the interpolant minus T in [s[j], s[j+1]] (Illinois false position
-// safeguarded by bisection), returned as lambda.
-GFD_D double interp_root(const double* s, const double* f, double T, int j) {
-  double wb[KNODES];
-#pragma unroll
-  for (int m = 0; m < KNODES; ++m) {
-    double p = 1.0;
-    for (int n = 0; n < KNODES; ++n)
-      if (n != m) p *= (s[m] - s[n]);
-    wb[m] = 1.0 / p;
+// 1/d in FP64 from an FP32 seed and two Newton steps (|d| within FP32 range).
+GFD_D double rcp_d(double d) {
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Root in s of the interpolant of (s_m, f_m) minus T inside [s_j, s_{j+1}]
+// (f increases through T there), as lambda = exp(s).  Lane m < KNODES holds
+// node m; the barycentric sums are warp reductions.  Safeguarded Newton:
+// steps leaving the bracket fall back to bisection.
+GFD_D double interp_root_warp(double sm, double fm, double T, int j, int lane) {
+  const bool own = lane < KNODES;
+  double prod = 1.0;
+  for (int n = 0; n < KNODES; ++n) {
+    const double sn = __shfl_sync(0xffffffffu, sm, n);
+    if (n != lane) prod *= (sm - sn);
   }
-  double a = s[j], b = s[j + 1];
-  double fa = f[j] - T, fb = f[j + 1] - T;
+  const double wb = own ? 1.0 / prod : 0.0;
+  double a = __shfl_sync(0xffffffffu, sm, j), b = __shfl_sync(0xffffffffu, sm, j + 1);
+  const double fa = __shfl_sync(0xffffffffu, fm, j) - T;
+  const double fb = __shfl_sync(0xffffffffu, fm, j + 1) - T;
   if (fa == 0.0) return exp(a);
   if (fb == 0.0) return exp(b);
-  int side = 0;
-  for (int it = 0; it < 100; ++it) {
-    double c = (fb * a - fa * b) / (fb - fa);
-    if (!(c > a && c < b)) c = 0.5 * (a + b);
-    const double fc = bary_eval(s, f, wb, c) - T;
-    if (fc == 0.0) return exp(c);
-    if ((fc < 0.0) == (fa < 0.0)) {
-      a = c;
-      fa = fc;
-      if (side == -1) fb *= 0.5;
-      side = -1;
-    } else {
-      b = c;
-      fb = fc;
-      if (side == 1) fa *= 0.5;
-      side = 1;
-    }
-    if (b - a <= 1e-15 * fmax(1.0, fabs(a))) break;
+  double x = a - fa * (b - a) / (fb - fa);
+  if (!(x > a && x < b)) x = 0.5 * (a + b);
+  for (int it = 0; it < 40; ++it) {
+    const double d = x - sm;
+    const unsigned hit = __ballot_sync(0xffffffffu, own && d == 0.0);
+    if (hit) return exp(x);  // x is a node; bracket ends already excluded roots there
+    const double rd = own ? rcp_d(d) : 0.0;
+    const double t = wb * rd;
+    const double N = warp_sum_full(t * fm);
+    const double D = warp_sum_full(t);
+    const double r = N / D;
+    const double dr = warp_sum_full(own ? t * (r - fm) * rd : 0.0) / D;
+    const double g = r - T;
+    if (g < 0.0)
+      a = x;
+    else
+      b = x;
+    double xn = x - g / dr;
+    if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
+    const double step = fabs(xn - x);
+    x = xn;
+    if (step <= 1e-15 * fmax(1.0, fabs(x)) || b - a <= 1e-15 * fmax(1.0, fabs(a))) break;
   }
-  return exp(0.5 * (a + b));
+  return exp(x);
 }
 
-GFD_D void resolve(ImgState* st, double lam, int iter, double* lam_out) {
-  st->lam = lam;
-  st->need = 0;
-  if (lam_out) lam_out[iter] = lam;
-  if (isfinite(lam) && lam > 0.0) set_bracket(st, lam / PRIMARY_RATIO, lam * PRIMARY_RATIO);
+GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int lane) {
+  if (lane == 0) {
+    st->lam = lam;
+    st->need = 0;
+    if (lam_out) lam_out[iter] = lam;
+  }
+  if (isfinite(lam) && lam > 0.0) set_bracket_warp(st, lam / PRIMARY_RATIO, lam * PRIMARY_RATIO, lane);
 }
 
-// Consume the accumulators of the pass that just completed for this image.
-// Run by one thread of the image's last block.
-GFD_D void lambda_update(ImgState* st, const double* tot, double P, bool primary,
-                         bool last_chance, int iter, double* lam_out, double* res_out) {
-  double f[KNODES];
-  for (int j = 0; j < KNODES; ++j) f[j] = tot[j] / P;
-  const double resinf = tot[KNODES] / P;
+// Consume the totals of the pass that just completed for this image (tot:
+// KNODES node sums and the residual sum, visible to the warp).  Run by the
+// 32 lanes of one warp of the image's last block; every lane takes the same
+// decisions from the same values.
+GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool primary,
+                              bool last_chance, int iter, double* lam_out, double* res_out,
+                              int lane) {
   const double T = st->T;
+  const double resinf = tot[KNODES] / P;
   if (primary) {
-    st->res = resinf;
-    if (res_out) res_out[iter] = resinf;
+    if (lane == 0) {
+      st->res = resinf;
+      if (res_out) res_out[iter] = resinf;
+    }
     if (!isfinite(resinf)) {
-      st->status |= ST_NONFINITE;
-      resolve(st, INFINITY, iter, lam_out);
+      if (lane == 0) st->status |= ST_NONFINITE;
+      resolve_warp(st, INFINITY, iter, lam_out, lane);
       return;
     }
     if (resinf <= T) {  // u_E in K (Sec. 3.2): lambda = inf, u_I = u_p = u_E
-      resolve(st, INFINITY, iter, lam_out);
+      resolve_warp(st, INFINITY, iter, lam_out, lane);
       return;
     }
     const double t = sqrt(T / resinf);
-    st->lam_up = fmin(1e30, st->amax * t / (1.0 - t));
+    if (lane == 0) st->lam_up = fmin(1e30, st->amax * t / (1.0 - t));
+    __syncwarp();
   }
-  double s[KNODES];
-  for (int j = 0; j < KNODES; ++j) s[j] = log((double)st->node[j]);
+  const double f0 = tot[0] / P, fK = tot[KNODES - 1] / P;
   const double lo = (double)st->node[0], hi = (double)st->node[KNODES - 1];
   bool open = true;
-  if (!(f[0] <= T)) {  // root below the bracket (or NaN)
-    if (!isfinite(f[0])) {
-      st->status |= ST_NONFINITE;
-      resolve(st, INFINITY, iter, lam_out);
+  if (!(f0 <= T)) {  // root below the bracket (or NaN)
+    if (!isfinite(f0)) {
+      if (lane == 0) st->status |= ST_NONFINITE;
+      resolve_warp(st, INFINITY, iter, lam_out, lane);
       return;
     }
     if (lo <= LAMBDA_LO * 1.000001) {
-      st->status |= ST_NONCONVERGED;
-      resolve(st, LAMBDA_LO, iter, lam_out);
+      if (lane == 0) st->status |= ST_NONCONVERGED;
+      resolve_warp(st, LAMBDA_LO, iter, lam_out, lane);
       return;
     }
-    set_bracket(st, LAMBDA_LO, lo);
-  } else if (f[KNODES - 1] < T) {  // root above the bracket
-    set_bracket(st, hi, fmax(st->lam_up, hi * 4.0));
+    set_bracket_warp(st, LAMBDA_LO, lo, lane);
+  } else if (fK < T) {  // root above the bracket
+    set_bracket_warp(st, hi, fmax(st->lam_up, hi * 4.0), lane);
   } else {
     int j = 0;
-    while (j < KNODES - 2 && f[j + 1] < T) ++j;
-    const double W = s[KNODES - 1] - s[0];
+    while (j < KNODES - 2 && tot[j + 1] / P < T) ++j;
+    const double sm = lane < KNODES ? st->snode[lane] : 0.0;
+    const double fm = lane < KNODES ? tot[lane] / P : 0.0;
+    const double W = st->snode[KNODES - 1] - st->snode[0];
     if (W <= W_EXACT) {
-      resolve(st, interp_root(s, f, T, j), iter, lam_out);
+      const double lam = interp_root_warp(sm, fm, T, j, lane);
+      resolve_warp(st, lam, iter, lam_out, lane);
       open = false;
     } else if (W <= W_ESTIMATE) {
-      const double est = interp_root(s, f, T, j);
-      set_bracket(st, est * (1.0 - EST_HALF_WIDTH), est * (1.0 + EST_HALF_WIDTH));
+      const double est = interp_root_warp(sm, fm, T, j, lane);
+      __syncwarp();
+      set_bracket_warp(st, est * (1.0 - EST_HALF_WIDTH), est * (1.0 + EST_HALF_WIDTH), lane);
     } else {
-      set_bracket(st, (double)st->node[j], (double)st->node[j + 1]);
+      const double nlo = (double)st->node[j], nhi = (double)st->node[j + 1];
+      __syncwarp();
+      set_bracket_warp(st, nlo, nhi, lane);
     }
   }
   if (open) {
-    st->need = 1;
+    if (lane == 0) st->need = 1;
     if (last_chance) {
-      st->status |= ST_NONCONVERGED;
-      resolve(st, sqrt(st->lo * st->hi), iter, lam_out);
+      if (lane == 0) st->status |= ST_NONCONVERGED;
+      const double mid = sqrt(st->lo * st->hi);
+      __syncwarp();
+      resolve_warp(st, mid, iter, lam_out, lane);
     }
   }
 }
