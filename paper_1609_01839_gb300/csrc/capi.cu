@@ -126,7 +126,7 @@ size_t part_doubles(int M, int N) {
 
 size_t image_ws_bytes(int M, int N) {
   const size_t P = (size_t)M * N;
-  return 5 * align256(P * sizeof(float)) + 4 * align256((size_t)M * sizeof(float2)) +
+  return 7 * align256(P * sizeof(float)) + 4 * align256((size_t)M * sizeof(float2)) +
          align256(part_doubles(M, N) * sizeof(double)) + align256((size_t)M * sizeof(double));
 }
 
@@ -212,6 +212,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
     cl.cd.N = sizes[ci].second;
     cl.cd.n_img = (int)members[ci].size();
     cl.cd.img0 = (int)pl.order.size();
+    cl.cd.TB = class_tile_width(cl.cd.M, cl.cd.N);
     cl.imgs = c->d_imgs;
     cl.st = c->d_st;
     cl.max_rad = 0;
@@ -235,6 +236,11 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
       float2** planes[5] = {&d.S, &d.QI, &d.Qp, &d.H, &d.Y};
       for (float2** pp : planes) {
         *pp = reinterpret_cast<float2*>(cur);
+        cur += align256(P * sizeof(float));
+      }
+      float** rplanes[2] = {&d.uI, &d.up};
+      for (float** pp : rplanes) {
+        *pp = reinterpret_cast<float*>(cur);
         cur += align256(P * sizeof(float));
       }
       float2** cols[4] = {&d.H0, &d.HN, &d.Y0, &d.YN};
@@ -285,8 +291,8 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     ++L;
   }
   for (auto& cl : pl.classes) {
-    GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_QI, s));
-    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_QI, SEL_S, false, s));
+    GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
+    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_UI, SEL_S, false, s));
     GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_H, false, s));
     GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_Y, SEL_S, false, s));
     GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_YS, false, s));
@@ -314,7 +320,8 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
       }
     for (auto& cl : pl.classes) {
       GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
-      GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, 1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
+      GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
+                                              1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
       GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
       L += 3;
     }
@@ -323,9 +330,9 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     const gfdeconv_image& u = pl.user[i];
     const size_t bytes = (size_t)u.M * u.N * sizeof(float);
     if (u.uI_out && pl.iters > 0)
-      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.uI_out, pl.h_imgs[i].QI, bytes, cudaMemcpyDeviceToDevice, s));
+      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.uI_out, pl.h_imgs[i].uI, bytes, cudaMemcpyDeviceToDevice, s));
     if (u.up_out && pl.iters > 0)
-      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.up_out, pl.h_imgs[i].Qp, bytes, cudaMemcpyDeviceToDevice, s));
+      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.up_out, pl.h_imgs[i].up, bytes, cudaMemcpyDeviceToDevice, s));
   }
   pl.launches = L;
   return cudaSuccess;
@@ -672,14 +679,14 @@ int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, 
   cudaError_t e = aux_slot(c, 0, &a);
   if (e != cudaSuccess) return map_err(e);
   ImgDesc d{};
-  d.QI = reinterpret_cast<float2*>(const_cast<float*>(I));
-  d.Qp = reinterpret_cast<float2*>(const_cast<float*>(p));
+  d.uI = const_cast<float*>(I);
+  d.up = const_cast<float*>(p);
   d.u = u_out;
   d.w = w;
   d.eps = eps;
   if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
   ClassLaunch cl{};
-  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
   cl.max_rad = (w - 1) / 2;
@@ -703,7 +710,7 @@ int gfdeconv_fft2_r2c(gfdeconv_ctx* c, const float* x, int M, int N, float* X, v
   d.Y = reinterpret_cast<float2*>(X);
   if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
   ClassLaunch cl{};
-  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
   const Tables t{c->tw, c->d2};
@@ -723,18 +730,18 @@ int gfdeconv_fft2_c2r(gfdeconv_ctx* c, const float* X, int M, int N, float* x, v
   if (e != cudaSuccess) return map_err(e);
   ImgDesc d{};
   d.QI = reinterpret_cast<float2*>(a->ws);
+  d.uI = x;
   if ((e = aux_upload(a, d, s)) != cudaSuccess) return map_err(e);
   if ((e = cudaMemcpyAsync(a->ws, X, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return map_err(e);
   ClassLaunch cl{};
-  cl.cd = ClassDesc{M, N, 1, 0};
+  cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
   const Tables t{c->tw, c->d2};
   if ((e = launch_col_plain(cl, t, SEL_QI, SEL_QI, true, s)) != cudaSuccess) return map_err(e);
-  if ((e = launch_row_c2r(cl, t, SEL_QI, -1, 1.0f / ((float)M * (float)N), s)) != cudaSuccess)
-    return map_err(e);
-  if ((e = cudaMemcpyAsync(x, a->ws, P * sizeof(float), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+  if ((e = launch_row_c2r(cl, t, SEL_QI, -1, SEL_UI, -1, 1.0f / ((float)M * (float)N), s)) !=
+      cudaSuccess)
     return map_err(e);
   return map_err(aux_finish(a, s));
 }

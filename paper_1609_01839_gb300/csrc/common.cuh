@@ -105,11 +105,14 @@ struct ImgDesc {
   int kh, kw, w, pad_;
   double sigma, eps, rho_fixed;
   // workspace planes (M*N/2 complex each)
+  // spectra are packed half spectra in the class's column-tiled layout
   float2* S;          // forward spectrum scratch (row pass output, then U_E)
-  float2* QI;         // U_I, then u_I (real, in place)
-  float2* Qp;         // U_p, then u_p (real, in place)
-  float2* H;          // PSF spectrum (packed)
-  float2* Y;          // observation spectrum (packed)
+  float2* QI;         // U_I (Eq. 8)
+  float2* Qp;         // U_p (Eq. 9)
+  float2* H;          // PSF spectrum
+  float2* Y;          // observation spectrum
+  float* uI;          // u_I, real M*N (row-major)
+  float* up;          // u_p, real M*N (row-major)
   float2* H0;         // H(k, 0),   k < M (unpacked DC column)
   float2* HN;         // H(k, N/2)
   float2* Y0;         // Y(k, 0)
@@ -121,6 +124,7 @@ struct ImgDesc {
 // One size class of a batch: all images with the same canvas M x N.
 struct ClassDesc {
   int M, N, n_img, img0;   // images img0 .. img0+n_img-1 of the batch
+  int TB;                  // tile width of the class's spectra (columns per tile)
 };
 
 }  // namespace gfd

@@ -1,11 +1,16 @@
 // 2-D real DFT passes and the spectral steps of the deblurring solve.
 //
-// Packed half-spectrum layout (M rows x N/2 complex): S[m][l] = X(m, l) for
-// 1 <= l < N/2 and S[m][0] = X(m, 0) + i X(m, N/2), X the full 2-D DFT.  A
+// Packed half spectrum (M rows x N/2 complex): S(m, l) = X(m, l) for
+// 1 <= l < N/2 and S(m, 0) = X(m, 0) + i X(m, N/2), X the full 2-D DFT.  A
 // row pass maps each real row to its packed row DFT; a column pass is a plain
 // complex FFT down every packed column (column 0 included, since its two real
 // row spectra pack into one complex signal).  Bins (m, 0) and (m, N/2) are
 // unpacked where a spectral formula needs them.
+//
+// Spectra are stored column-tiled: S(m, l) at (l / TB) * M * TB + m * TB +
+// l % TB, TB the class's tile width.  A column item (TB columns, all M rows)
+// is then one contiguous block of memory, and a row item (rpc rows) writes a
+// contiguous run of rpc * TB values per tile.  TB = N/2 is plain row-major.
 #include "fft.cuh"
 #include "lambda.cuh"
 #include "launch.h"
@@ -20,6 +25,8 @@ GFD_D float* real_plane(const ImgDesc& d, int sel) {
     case SEL_QI: return reinterpret_cast<float*>(d.QI);
     case SEL_QP: return reinterpret_cast<float*>(d.Qp);
     case SEL_H: return reinterpret_cast<float*>(d.H);
+    case SEL_UI: return d.uI;
+    case SEL_UP: return d.up;
     default: return reinterpret_cast<float*>(d.Y);
   }
 }
@@ -36,31 +43,33 @@ constexpr int threads_per_team(int L) { return L / radix_for(L); }
 // flight while the block computes.
 
 // ---------------------------------------------------------------------------
-// Row pass, forward: real rows -> packed row spectra.  An item is rpc
-// consecutive rows of one image (a contiguous block of memory).
-// Each row of N reals is read as N/2 complex z[n] = x[2n] + i x[2n+1];
-// Z = FFT_{N/2}(z); then X[k] = (Z[k] + conj Z[-k])/2 + W_N^k (Z[k] - conj Z[-k])/(2i)
-// and X[0], X[N/2] = Re Z[0] +- Im Z[0] (packed as X[0] + i X[N/2]).
+// Row pass, forward: real rows -> packed row spectra (tiled).  An item is
+// rpc consecutive rows of one image.  Each row of N reals is read as N/2
+// complex z[n] = x[2n] + i x[2n+1]; Z = FFT_{N/2}(z); then
+// X[k] = (Z[k] + conj Z[-k])/2 + W_N^k (Z[k] - conj Z[-k])/(2i), and
+// X[0], X[N/2] = Re Z[0] +- Im Z[0] (packed as X[0] + i X[N/2]).
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs,
-                                                 ImgState* st, const float2* __restrict__ tw,
-                                                 int rpc, int src_sel, int dst_sel, int do_sum) {
+__global__ void __launch_bounds__(256, 2)
+k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restrict__ tw, int rpc,
+          int src_sel, int dst_sel, int do_sum) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(L), T = threads_per_team(L);
   constexpr int N = 2 * L;
+  const int TB = cd.TB, M = cd.M;
   const int item_elems = rpc * L;
   float2* land = smem;
-  float2* work = smem + item_elems;
-  double* red = reinterpret_cast<double*>(work + rpc * team_stride(L));
+  float2* work = land + item_elems;
+  float2* outb = work + rpc * team_stride(L);
+  double* red = reinterpret_cast<double*>(outb + item_elems);
   const int team = threadIdx.x / T, j = threadIdx.x % T;
-  const int n_items = cd.n_img * cd.M / rpc;
+  const int n_items = cd.n_img * M / rpc;
   auto issue = [&](int item) {
     if (item < n_items) {
       const int row_c = item * rpc;
-      const ImgDesc& d = imgs[cd.img0 + row_c / cd.M];
+      const ImgDesc& d = imgs[cd.img0 + row_c / M];
       const float2* src =
-          reinterpret_cast<const float2*>(real_plane(d, src_sel)) + (size_t)(row_c % cd.M) * L;
+          reinterpret_cast<const float2*>(real_plane(d, src_sel)) + (size_t)(row_c % M) * L;
       for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x)
         cp_async16(land + 2 * c, src + 2 * c);
     }
@@ -70,9 +79,8 @@ __global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc*
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     cp_async_wait<0>();
     __syncthreads();
-    const int row_c = item * rpc + team;
-    const int li = row_c / cd.M, row = row_c % cd.M;
-    const ImgDesc& d = imgs[cd.img0 + li];
+    const int row0 = (item * rpc) % M;
+    const ImgDesc& d = imgs[cd.img0 + (item * rpc) / M];
     float2* buf = work + team * team_stride(L);
     const float2* in = land + team * L;
     if (do_sum) {
@@ -90,9 +98,9 @@ __global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc*
     if (do_sum && threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < num_warps(); ++w) s += red[w];
-      d.rowsum[row / rpc] = s;  // one partial per item, summed by the column pass
+      d.rowsum[row0 / rpc] = s;  // one partial per item, summed by the column pass
     }
-    float2* dst = cplx_plane(d, dst_sel) + (size_t)row * L;
+    float2* ob = outb + team * L;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int k = j + i * T;
@@ -107,48 +115,59 @@ __global__ void __launch_bounds__(256, 3) k_row_r2c(ClassDesc cd, const ImgDesc*
         const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
         out = cadd(E, cmul(__ldg(&tw[k * (TW_N / N)]), O));
       }
-      dst[k] = out;
+      ob[k] = out;
+    }
+    __syncthreads();
+    // copy out tile by tile: rows row0 .. row0+rpc-1 of tile t are contiguous
+    float2* dst = cplx_plane(d, dst_sel);
+    const int per_tile = rpc * TB / 2;  // 16-byte chunks
+    for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x) {
+      const int t = c / per_tile, w = c - t * per_tile;
+      const int r = w / (TB / 2), q = w - r * (TB / 2);
+      const float4 v = *reinterpret_cast<const float4*>(outb + r * L + t * TB + 2 * q);
+      *reinterpret_cast<float4*>(dst + (size_t)t * M * TB + (size_t)(row0 + r) * TB + 2 * q) = v;
     }
   }
   cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
-// Row pass, inverse, in place: packed row spectra -> real rows (scaled).
+// Row pass, inverse: packed row spectra (tiled) -> real rows (scaled).
 // Z[k] = (R[k] + conj R[L-k]) + i (R[k] - conj R[L-k]) W_N^{-k}, with
 // R[0], R[N/2] the real and imaginary parts of the packed entry 0; the
 // unnormalised inverse FFT of Z gives x[2n] + i x[2n+1] times N.
-// Items cover the rows of plane sel0, then of plane sel1 (if >= 0).
+// Items cover spectrum sel0 -> real plane dsel0, then sel1 -> dsel1.
 // ---------------------------------------------------------------------------
 template <int L>
-__global__ void __launch_bounds__(256, 3) k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs,
-                                                 const float2* __restrict__ tw, int rpc, int sel0,
-                                                 int sel1, float scale) {
+__global__ void __launch_bounds__(256, 3)
+k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restrict__ tw, int rpc,
+          int sel0, int sel1, int dsel0, int dsel1, float scale) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(L), T = threads_per_team(L);
   constexpr int N = 2 * L;
+  const int TB = cd.TB, M = cd.M;
   const int item_elems = rpc * L;
   float2* land = smem;
   float2* work = smem + item_elems;
   const int team = threadIdx.x / T, j = threadIdx.x % T;
-  const int per_plane = cd.n_img * cd.M / rpc;
+  const int per_plane = cd.n_img * M / rpc;
   const int n_items = sel1 >= 0 ? 2 * per_plane : per_plane;
-  auto rows_of = [&](int item, int& sel, int& row_c) {
-    sel = sel0;
-    if (item >= per_plane) {
-      item -= per_plane;
-      sel = sel1;
-    }
-    row_c = item * rpc;
-  };
+  const int per_tile = rpc * TB / 2;
   auto issue = [&](int item) {
     if (item < n_items) {
-      int sel, row_c;
-      rows_of(item, sel, row_c);
-      const ImgDesc& d = imgs[cd.img0 + row_c / cd.M];
-      const float2* src = cplx_plane(d, sel) + (size_t)(row_c % cd.M) * L;
-      for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x)
-        cp_async16(land + 2 * c, src + 2 * c);
+      int sel = sel0;
+      if (item >= per_plane) {
+        item -= per_plane;
+        sel = sel1;
+      }
+      const int row_c = item * rpc;
+      const ImgDesc& d = imgs[cd.img0 + row_c / M];
+      const float2* src = cplx_plane(d, sel) + (size_t)(row_c % M) * TB;
+      for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x) {
+        const int t = c / per_tile, w = c - t * per_tile;
+        const int r = w / (TB / 2), q = w - r * (TB / 2);
+        cp_async16(land + r * L + t * TB + 2 * q, src + (size_t)t * M * TB + r * TB + 2 * q);
+      }
     }
     cp_async_commit();
   };
@@ -156,10 +175,13 @@ __global__ void __launch_bounds__(256, 3) k_row_c2r(ClassDesc cd, const ImgDesc*
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     cp_async_wait<0>();
     __syncthreads();
-    int sel, row_c0;
-    rows_of(item, sel, row_c0);
-    const int row_c = row_c0 + team;
-    const int li = row_c / cd.M, row = row_c % cd.M;
+    int it = item, dsel = dsel0;
+    if (it >= per_plane) {
+      it -= per_plane;
+      dsel = dsel1;
+    }
+    const int row_c = it * rpc + team;
+    const int li = row_c / M, row = row_c % M;
     const ImgDesc& d = imgs[cd.img0 + li];
     float2* buf = work + team * team_stride(L);
     const float2* in = land + team * L;
@@ -185,7 +207,7 @@ __global__ void __launch_bounds__(256, 3) k_row_c2r(ClassDesc cd, const ImgDesc*
     __syncthreads();
     issue(item + gridDim.x);
     fft_team<L, true>(buf, j, tw);
-    float2* rowp = cplx_plane(d, sel) + (size_t)row * L;
+    float2* rowp = reinterpret_cast<float2*>(real_plane(d, dsel)) + (size_t)row * L;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int n = j + i * T;
@@ -196,44 +218,48 @@ __global__ void __launch_bounds__(256, 3) k_row_c2r(ClassDesc cd, const ImgDesc*
 }
 
 // ---------------------------------------------------------------------------
-// Column passes.  An item is B adjacent packed columns of one image; it lands
-// as an interleaved [M][B] tile (a warp's copies cover B consecutive complex
-// values of consecutive rows), and team b (threads b, b+B, ...) transforms
-// column c0+b.
+// Column passes.  An item is B adjacent packed columns of one image (B = TB
+// in the iteration kernels: one contiguous tile).  It lands as an [M][B]
+// tile and team b (threads b, b+B, ...) transforms column c0+b.
 // ---------------------------------------------------------------------------
+
+// copy rows 0..M-1 of B columns (row stride TB) into an [M][B] shared tile;
+// a single contiguous block when B == TB.
+GFD_D void issue_tile(float2* dst, const float2* src, int M, int TB, int B) {
+  const int per_row = B / 2;  // 16-byte chunks per row segment
+  for (int c = threadIdx.x; c < M * per_row; c += blockDim.x) {
+    const int a = c / per_row, q = c - a * per_row;
+    cp_async16(dst + a * B + 2 * q, src + (size_t)a * TB + 2 * q);
+  }
+}
+
+// Setup / utility column FFT (not pipelined): plane src -> dst, in place
+// allowed; B columns (inside one tile) per block.
 template <int M, bool INV>
 __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
                             const float2* __restrict__ tw, int B, int src_sel, int dst_sel) {
   extern __shared__ float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
-  const int Lc = cd.N / 2;
+  const int Lc = cd.N / 2, TB = cd.TB;
   const int cpi = Lc / B;
   const ImgDesc& d = imgs[cd.img0 + blockIdx.x / cpi];
   const int c0 = (blockIdx.x % cpi) * B;
-  const int b = threadIdx.x & (B - 1), j = threadIdx.x / B;
+  const int b = threadIdx.x % B, j = threadIdx.x / B;
+  const size_t off = (size_t)(c0 / TB) * M * TB + (c0 % TB) + b;
   float2* buf = smem + b * team_stride(M);
-  const float2* src = cplx_plane(d, src_sel) + c0 + b;
-  float2* dst = cplx_plane(d, dst_sel) + c0 + b;
+  const float2* src = cplx_plane(d, src_sel) + off;
+  float2* dst = cplx_plane(d, dst_sel) + off;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int a = j + i * T;
-    buf[phys(a)] = src[(size_t)a * Lc];
+    buf[phys(a)] = src[(size_t)a * TB];
   }
   __syncthreads();
   fft_team<M, INV>(buf, j, tw);
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int k = j + i * T;
-    dst[(size_t)k * Lc] = buf[phys(out_pos<M>(k))];
-  }
-}
-
-// copy B packed columns (rows 0..M-1) of plane p into an [M][B] tile
-GFD_D void issue_cols(float2* tile, const float2* plane, int M, int Lc, int B, int c0) {
-  const int per_row = B / 2;  // 16-byte chunks per row segment
-  for (int c = threadIdx.x; c < M * per_row; c += blockDim.x) {
-    const int a = c / per_row, q = c - a * per_row;
-    cp_async16(tile + a * B + 2 * q, plane + (size_t)a * Lc + c0 + 2 * q);
+    dst[(size_t)k * TB] = buf[phys(out_pos<M>(k))];
   }
 }
 
@@ -246,25 +272,40 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 }
 
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
-// the first evaluation of Eq. 11 at the nodes of the image's bracket.
+// the first evaluation of Eq. 11 at the nodes of the image's bracket.  The S,
+// H and Y tiles of the next item land while the current one is processed
+// (S only for M = 4096, where three landing tiles do not fit).
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
-                 const float2* __restrict__ tw, int B, int iter, int row_items) {
+                 const float2* __restrict__ tw, int iter, int row_items) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
+  constexpr bool HY_LAND = M < 4096;
   __shared__ float s_nodes[KNODES];
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
+  const int B = cd.TB;
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
   const int n_items = cd.n_img * cpi;
-  float2* land = smem;
-  float2* work = smem + M * B;
+  const int tile = M * B;
+  float2* landS = smem;
+  float2* landH = landS + tile;
+  float2* landY = landH + tile;
+  float2* work = HY_LAND ? landY + tile : landH;
   double* red = reinterpret_cast<double*>(work + B * team_stride(M));
-  const int b = threadIdx.x & (B - 1), j = threadIdx.x / B;
+  const int b = threadIdx.x % B, j = threadIdx.x / B;
   auto issue = [&](int item) {
-    if (item < n_items) issue_cols(land, imgs[cd.img0 + item / cpi].S, M, Lc, B, (item % cpi) * B);
+    if (item < n_items) {
+      const ImgDesc& d = imgs[cd.img0 + item / cpi];
+      const size_t off = (size_t)(item % cpi) * tile;
+      issue_tile(landS, d.S + off, M, B, B);
+      if constexpr (HY_LAND) {
+        issue_tile(landH, d.H + off, M, B, B);
+        issue_tile(landY, d.Y + off, M, B, B);
+      }
+    }
     cp_async_commit();
   };
   issue(blockIdx.x);
@@ -274,36 +315,40 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     const int gi = cd.img0 + item / cpi;
     const ImgDesc& d = imgs[gi];
     ImgState* S = st + gi;
-    const int c0 = (item % cpi) * B;
-    const int col = c0 + b;
+    const int t = item % cpi;
+    const int col = t * B + b;
+    const size_t off = (size_t)t * tile;
     for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
-    float2* buf = work + b * team_stride(M);
-    fft_team_from<M, false>(land + b, StridedIdx{B}, buf, j, tw);
-    issue(item + gridDim.x);
-    if (c0 == 0) {  // the DC bin needs sum(u_E): total of the row pass's partials
+    if (t == 0) {  // the DC bin needs sum(u_E): total of the row pass's partials
       block_sum_columns(d.rowsum, row_items, 1, 1, red, s_tot);
       if (threadIdx.x == 0) S->sum_u = s_tot[0];
     }
-    float2* spec = d.S + col;
+    float2* buf = work + b * team_stride(M);
+    fft_team_from<M, false>(landS + b, StridedIdx{B}, buf, j, tw);  // ends synchronised
     float nodes[KNODES];
 #pragma unroll
     for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
     float acc[KNODES + 1];
 #pragma unroll
     for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
+    float2* spec = d.S + off + b;
     if (col != 0) {
-      const float2* Hc = d.H + col;
-      const float2* Yc = d.Y + col;
 #pragma unroll 4
       for (int i = 0; i < R; ++i) {
         const int k = j + i * T;
-        const float2 H = __ldg(&Hc[(size_t)k * Lc]);
-        const float2 Y = __ldg(&Yc[(size_t)k * Lc]);
+        float2 Hk, Yk;
+        if constexpr (HY_LAND) {
+          Hk = landH[k * B + b];
+          Yk = landY[k * B + b];
+        } else {
+          Hk = __ldg(&d.H[off + (size_t)k * B + b]);
+          Yk = __ldg(&d.Y[off + (size_t)k * B + b]);
+        }
         const float2 U = buf[phys(out_pos<M>(k))];
-        spec[(size_t)k * Lc] = U;
-        const float2 r = csub(cmul(H, U), Y);
+        spec[(size_t)k * B] = U;
+        const float2 r = csub(cmul(Hk, U), Yk);
         const float rr = fmaf(r.x, r.x, r.y * r.y);
-        const float a = fmaf(H.x, H.x, H.y * H.y);
+        const float a = fmaf(Hk.x, Hk.x, Hk.y * Hk.y);
         accum_bin(2.0f * rr, a, nodes, acc);  // bins l and N-l
       }
     } else {
@@ -329,10 +374,11 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         const float2 rb = csub(cmul(HB, UB), YB);
         accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
         accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
-        spec[(size_t)k * Lc] = U;
+        spec[(size_t)k * B] = U;
       }
     }
-    block_partials(acc, red, d.part + (size_t)(item % cpi) * (KNODES + 1));
+    block_partials(acc, red, d.part + (size_t)t * (KNODES + 1));  // ends synchronised
+    issue(item + gridDim.x);  // every landing tile of this item is consumed
     if (last_item(&S->cta_done, cpi, &s_flag)) {
       block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
       if (threadIdx.x < 32)
@@ -348,15 +394,17 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
 }
 
 // Fallback evaluation of Eq. 11 over the stored spectrum U_E for images whose
-// root is still open; a block covers `chunk` packed elements of one image.
-__global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
-                              int chunk, int iter, int last_chance) {
+// root is still open; a block covers `chunk` elements (in tiled order) of one
+// image.
+__global__ void __launch_bounds__(256)
+k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int chunk, int iter,
+              int last_chance) {
   __shared__ float s_nodes[KNODES];
   __shared__ double red[32 * (KNODES + 1)];
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
-  const int Lc = cd.N / 2;
-  const int per_img = cd.M * Lc;
+  const int Lc = cd.N / 2, TB = cd.TB, M = cd.M;
+  const int per_img = M * Lc;
   const int cpi = per_img / chunk;
   const int gi = cd.img0 + blockIdx.x / cpi;
   ImgState* S = st + gi;
@@ -371,16 +419,18 @@ __global__ void __launch_bounds__(256) k_lambda_pass(ClassDesc cd, const ImgDesc
 #pragma unroll
   for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
   const int e0 = (blockIdx.x % cpi) * chunk;
-  const int M = cd.M;
+  const int tile = M * TB;
   for (int e = e0 + threadIdx.x; e < e0 + chunk; e += blockDim.x) {
-    const int k = e / Lc, col = e - k * Lc;
+    const int t = e / tile, rem = e - t * tile;
+    const int k = rem / TB, b = rem - k * TB;
+    const int col = t * TB + b;
     const float2 U = d.S[e];
     if (col != 0) {
       const float2 H = __ldg(&d.H[e]), Y = __ldg(&d.Y[e]);
       const float2 r = csub(cmul(H, U), Y);
       accum_bin(2.0f * fmaf(r.x, r.x, r.y * r.y), fmaf(H.x, H.x, H.y * H.y), nodes, acc);
     } else {
-      const float2 Um = d.S[(size_t)((M - k) & (M - 1)) * Lc];
+      const float2 Um = d.S[(size_t)((M - k) & (M - 1)) * TB];
       float2 UA, UB;
       unpack_pair(U, Um, UA, UB);
       const float2 HA = d.H0[k], HB = d.HN[k], YA = d.Y0[k], YB = d.YN[k];
@@ -435,34 +485,34 @@ GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool bra
 }
 
 // Spectral solves fused with the inverse column FFTs: an item's U_E, H and Y
-// columns land together (U_E only for M = 4096, where three landing tiles
-// would not fit beside the work tiles; H and Y are then read directly);
-// Eq. 8 and 9 fill two work tiles (U_I, U_p) that are inverse-transformed
-// while the next item's columns are fetched.
+// tiles land together (U_E only for M = 4096); Eq. 8 and 9 fill two work
+// tiles (U_I, U_p) that are inverse-transformed while the next item's tiles
+// are fetched.
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st,
-                const float2* __restrict__ tw, const float* __restrict__ d2tab, int B) {
+                const float2* __restrict__ tw, const float* __restrict__ d2tab) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
-  const int N = cd.N, Lc = N / 2;
+  constexpr bool HY_LAND = M < 4096;
+  const int N = cd.N, Lc = N / 2, B = cd.TB;
   const int cpi = Lc / B;
   const int n_items = cd.n_img * cpi;
-  constexpr bool HY_LAND = M < 4096;
+  const int tile = M * B;
   float2* landU = smem;
-  float2* landH = landU + M * B;
-  float2* landY = landH + M * B;
-  float2* workI = HY_LAND ? landY + M * B : landH;
+  float2* landH = landU + tile;
+  float2* landY = landH + tile;
+  float2* workI = HY_LAND ? landY + tile : landH;
   float2* workP = workI + B * team_stride(M);
-  const int b = threadIdx.x & (B - 1), j = threadIdx.x / B;
+  const int b = threadIdx.x % B, j = threadIdx.x / B;
   auto issue = [&](int item) {
     if (item < n_items) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
-      const int c0 = (item % cpi) * B;
-      issue_cols(landU, d.S, M, Lc, B, c0);
+      const size_t off = (size_t)(item % cpi) * tile;
+      issue_tile(landU, d.S + off, M, B, B);
       if constexpr (HY_LAND) {
-        issue_cols(landH, d.H, M, Lc, B, c0);
-        issue_cols(landY, d.Y, M, Lc, B, c0);
+        issue_tile(landH, d.H + off, M, B, B);
+        issue_tile(landY, d.Y + off, M, B, B);
       }
     }
     cp_async_commit();
@@ -474,8 +524,9 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     __syncthreads();
     const int gi = cd.img0 + item / cpi;
     const ImgDesc& d = imgs[gi];
-    const int c0 = (item % cpi) * B;
-    const int col = c0 + b;
+    const int t = item % cpi;
+    const int col = t * B + b;
+    const size_t off = (size_t)t * tile;
     const double lamd = __ldcg(&st[gi].lam);
     const bool branch = !(lamd < 1e300);
     const float lam = branch ? 0.0f : (float)lamd;
@@ -495,8 +546,8 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
           Hv = landH[e];
           Yv = landY[e];
         } else {
-          Hv = __ldg(&d.H[(size_t)k * Lc + col]);
-          Yv = __ldg(&d.Y[(size_t)k * Lc + col]);
+          Hv = __ldg(&d.H[off + e]);
+          Yv = __ldg(&d.Y[off + e]);
         }
         solve_bin(U, Hv, Yv, lam, d2r + d2c, branch, UI, Up);
       } else {
@@ -515,14 +566,14 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     issue(item + gridDim.x);
     fft_team<M, true>(bufI, j, tw);
     fft_team<M, true>(bufP, j, tw);
-    float2* qi = d.QI + col;
-    float2* qp = d.Qp + col;
+    float2* qi = d.QI + off + b;
+    float2* qp = d.Qp + off + b;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int k = j + i * T;
       const int p = phys(out_pos<M>(k));
-      qi[(size_t)k * Lc] = bufI[p];
-      qp[(size_t)k * Lc] = bufP[p];
+      qi[(size_t)k * B] = bufI[p];
+      qp[(size_t)k * B] = bufP[p];
     }
   }
   cp_async_wait<0>();
@@ -531,7 +582,6 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
 // ---------------------------------------------------------------------------
 // launch configuration and dispatch
 // ---------------------------------------------------------------------------
-// Largest block the kernel can be launched with (registers permitting).
 template <class K>
 static int max_threads(K kernel) {
   static int cached = 0;
@@ -574,18 +624,24 @@ static int rows_per_item(int L, int M) {
   return r;
 }
 
-static int cols_per_item(int M, int Lc, int threads, int max_thr) {
-  const int T = threads_per_team(M);
-  if (threads > max_thr) threads = max_thr;
+// Tile width of a class's spectra = columns per column item: a block of about
+// g_tiles.col_threads threads (512 for M = 4096), at least 2 columns (16-byte
+// copies), at most N/2.
+int class_tile_width(int M, int N) {
+  const int T = M / radix_for(M);
+  const int threads = M >= 4096 ? 512 : g_tiles.col_threads;
   int B = threads / T;
-  if (B < 2) B = 2;  // 16-byte copy chunks hold two columns
-  if (B > Lc) B = Lc;
+  if (B < 2) B = 2;
+  if (B > N / 2) B = N / 2;
   return B;
 }
 
-static size_t row_smem(int L, int rpc) {
-  return (size_t)rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
+static size_t row_r2c_smem(int L, int rpc) {
+  return (size_t)2 * rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
          32 * sizeof(double);
+}
+static size_t row_c2r_smem(int L, int rpc) {
+  return (size_t)rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2);
 }
 
 #define GFD_CASE_L(F, ...)             \
@@ -618,9 +674,9 @@ static void do_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst, 
   const int rpc = rows_per_item(L, c.cd.M);
   const int n_items = c.cd.n_img * c.cd.M / rpc;
   const int thr = rpc * threads_per_team(L);
-  const size_t smem = row_smem(L, rpc);
+  const size_t smem = row_r2c_smem(L, rpc);
   const int grid = persistent_grid(k_row_r2c<L>, thr, smem, n_items);
-  k_row_r2c<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, rpc, src, dst, sum);
+  k_row_r2c<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, src, dst, sum);
 }
 
 cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst,
@@ -633,21 +689,21 @@ cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int d
 }
 
 template <int L>
-static void do_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, float scale,
-                       cudaStream_t s) {
+static void do_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
+                       int dsel1, float scale, cudaStream_t s) {
   const int rpc = rows_per_item(L, c.cd.M);
   int n_items = c.cd.n_img * c.cd.M / rpc;
   if (sel1 >= 0) n_items *= 2;
   const int thr = rpc * threads_per_team(L);
-  const size_t smem = row_smem(L, rpc);
+  const size_t smem = row_c2r_smem(L, rpc);
   const int grid = persistent_grid(k_row_c2r<L>, thr, smem, n_items);
-  k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, scale);
+  k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, dsel0, dsel1, scale);
 }
 
-cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1,
-                           float scale, cudaStream_t s) {
+cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
+                           int dsel1, float scale, cudaStream_t s) {
   switch (c.cd.N / 2) {
-    GFD_CASE_L(do_row_c2r, c, t, sel0, sel1, scale, s)
+    GFD_CASE_L(do_row_c2r, c, t, sel0, sel1, dsel0, dsel1, scale, s)
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -657,17 +713,18 @@ template <int M>
 static void do_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst, bool inv,
                          cudaStream_t s) {
   const int Lc = c.cd.N / 2;
-  int B = 512 / threads_per_team(M);
+  const int T = threads_per_team(M);
   const int mt = inv ? max_threads(k_col_plain<M, true>) : max_threads(k_col_plain<M, false>);
-  if (B * threads_per_team(M) > mt) B = mt / threads_per_team(M);
+  int B = (mt < 512 ? mt : 512) / T;
   if (B < 1) B = 1;
   if (B > Lc) B = Lc;
+  if (B > c.cd.TB) B = c.cd.TB;  // a block stays inside one tile
   const size_t smem = (size_t)B * team_stride(M) * sizeof(float2);
   const int nblk = c.cd.n_img * (Lc / B);
   if (inv)
-    k_col_plain<M, true><<<nblk, B * threads_per_team(M), smem, s>>>(c.cd, c.imgs, t.tw, B, src, dst);
+    k_col_plain<M, true><<<nblk, B * T, smem, s>>>(c.cd, c.imgs, t.tw, B, src, dst);
   else
-    k_col_plain<M, false><<<nblk, B * threads_per_team(M), smem, s>>>(c.cd, c.imgs, t.tw, B, src, dst);
+    k_col_plain<M, false><<<nblk, B * T, smem, s>>>(c.cd, c.imgs, t.tw, B, src, dst);
 }
 
 cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst,
@@ -680,17 +737,21 @@ cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int
 }
 
 template <int M>
+static size_t col_smem(int B, int landings, int works, int nthr) {
+  return (size_t)landings * M * B * sizeof(float2) +
+         (size_t)works * B * team_stride(M) * sizeof(float2) +
+         (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
+}
+
+template <int M>
 static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
-  const int Lc = c.cd.N / 2;
-  const int B = cols_per_item(M, Lc, M >= 4096 ? 512 : g_tiles.col_threads,
-                              max_threads(k_col_fwd_lambda<M>));
+  const int Lc = c.cd.N / 2, B = c.cd.TB;
   const int nthr = B * threads_per_team(M);
-  const size_t smem = (size_t)M * B * sizeof(float2) + (size_t)B * team_stride(M) * sizeof(float2) +
-                      (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
+  const size_t smem = col_smem<M>(B, M < 4096 ? 3 : 1, 1, nthr);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items);
   const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M);
-  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, B, iter, row_items);
+  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, iter, row_items);
 }
 
 cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter,
@@ -713,15 +774,12 @@ cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
 
 template <int M>
 static void do_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {
-  const int Lc = c.cd.N / 2;
-  const int B = cols_per_item(M, Lc, M >= 4096 ? 512 : g_tiles.solve_threads,
-                              max_threads(k_col_solve_inv<M>));
+  const int Lc = c.cd.N / 2, B = c.cd.TB;
   const int nthr = B * threads_per_team(M);
-  const size_t smem = (size_t)(M < 4096 ? 3 : 1) * M * B * sizeof(float2) +
-                      (size_t)2 * B * team_stride(M) * sizeof(float2);
+  const size_t smem = col_smem<M>(B, M < 4096 ? 3 : 1, 2, 0);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_solve_inv<M>, nthr, smem, n_items);
-  k_col_solve_inv<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, t.d2, B);
+  k_col_solve_inv<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, t.d2);
 }
 
 cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {

@@ -205,8 +205,8 @@ k_guided_filter(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, in
   const ImgDesc& d = imgs[gi];
   const int M = cd.M, N = cd.N;
   const int y0 = blockIdx.y * GF_T, x0 = blockIdx.x * GF_T;
-  const float* I = reinterpret_cast<const float*>(d.QI);
-  const float* p = reinterpret_cast<const float*>(d.Qp);
+  const float* I = d.uI;
+  const float* p = d.up;
   const float* uo = (iter >= 0 && d.isnr_out) ? d.uo : nullptr;
   const float eps = (float)d.eps;
   const bool shifted = plain_var == 0;

@@ -111,7 +111,7 @@ __global__ void k_embed_psf(ClassDesc cd, const ImgDesc* __restrict__ imgs, int 
     float s = 0.0f;
     for (int a = (i + rh) % cd.M; a < d.kh; a += cd.M)
       for (int b = (j + rw) % cd.N; b < d.kw; b += cd.N) s += d.h[a * d.kw + b];
-    float* dst = dst_sel == SEL_QI ? reinterpret_cast<float*>(d.QI) : reinterpret_cast<float*>(d.S);
+    float* dst = dst_sel == SEL_UI ? d.uI : d.up;
     dst[rem] = s;
   }
 }
@@ -121,12 +121,12 @@ __global__ void k_embed_psf(ClassDesc cd, const ImgDesc* __restrict__ imgs, int 
 __global__ void k_unpack_dc(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st) {
   const int gi = cd.img0 + blockIdx.y;
   const ImgDesc& d = imgs[gi];
-  const int M = cd.M, Lc = cd.N / 2;
+  const int M = cd.M, TB = cd.TB;  // column 0 is column 0 of tile 0
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
   const int km = (M - k) & (M - 1);
-  const float2 hk = d.H[(size_t)k * Lc], hm = d.H[(size_t)km * Lc];
-  const float2 yk = d.Y[(size_t)k * Lc], ym = d.Y[(size_t)km * Lc];
+  const float2 hk = d.H[(size_t)k * TB], hm = d.H[(size_t)km * TB];
+  const float2 yk = d.Y[(size_t)k * TB], ym = d.Y[(size_t)km * TB];
   float2 A, B;
   {
     const float2 c = cconj(hm);

@@ -14,6 +14,8 @@ enum PlaneSel : int {
   SEL_QP = 4,  // U_p then u_p
   SEL_H = 5,   // PSF spectrum
   SEL_YS = 6,  // observation spectrum
+  SEL_UI = 7,  // u_I (real)
+  SEL_UP = 8,  // u_p (real)
 };
 
 // Tile shapes of the pass kernels (threads per block, which fixes rows per
@@ -42,9 +44,12 @@ struct ClassLaunch {
 // do_sum: accumulate the FP64 sum of src into st.sum_u.
 cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst,
                            bool do_sum, cudaStream_t s);
-// Inverse row pass, in place on one or two planes (sel1 < 0: one plane).
-cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1,
-                           float scale, cudaStream_t s);
+// Inverse row pass: spectrum sel0 -> real plane dsel0 (and sel1 -> dsel1
+// unless sel1 < 0), outputs scaled by `scale`.
+cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
+                           int dsel1, float scale, cudaStream_t s);
+// Tile width (columns per tile) of the spectra of an M x N class.
+int class_tile_width(int M, int N);
 // Plain column FFT src -> dst (in place allowed), forward or inverse.
 cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst,
                              bool inverse, cudaStream_t s);
@@ -56,7 +61,7 @@ cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
                                cudaStream_t s);
 // Spectral solves (Eq. 8, 9) fused with the inverse column FFTs: S -> QI, Qp.
 cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s);
-// Guided filter (Eq. 3-5): (QI, Qp) real planes -> u.  iter < 0: no ISNR.
+// Guided filter (Eq. 3-5): real planes (uI, up) -> u.  iter < 0: no ISNR.
 cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var,
                                  cudaStream_t s);
 // Setup kernels.
