@@ -78,12 +78,13 @@ struct ImgState {
   double den_isnr;   // ||y - u_orig||^2
   double lam;        // lambda of the current iteration (inf: branch u_E in K)
   double lo, hi;     // bracket of the nodes of the next pass
+  double invT;       // 1 / T
+  int mode;          // node layout of the next pass: 0 geometric, 1 Chebyshev in lambda
   double lam_up;     // upper bound of the root from res and amax
   double res;        // ||h*u_E - y||^2 of the current iteration
   double sum_u;      // FP64 sum of the current iterate u_E (its DC bin)
   double d00;        // DC residual sum(h) sum(u_E) - sum(y), FP64
   double err2;       // FP64 sum (u - u_orig)^2
-  double snode[KNODES];// exact log of each node value (the interpolation abscissae)
   float node[KNODES];// node values lambda_j (float) of the pending pass
   unsigned int cta_done;   // items of the current spectral pass completed
   unsigned int gf_done;    // last-block-done counter (guided filter)

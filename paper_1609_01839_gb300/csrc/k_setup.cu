@@ -92,6 +92,7 @@ __global__ void k_setup_init(ClassDesc cd, const ImgDesc* __restrict__ imgs, Img
   }
   S->rho = rho;
   S->T = rho * P * sig2;
+  S->invT = 1.0 / S->T;
   S->lam = NAN;
   S->need = 0;
   set_bracket(S, INITIAL_LO, INITIAL_HI);

@@ -7,74 +7,69 @@
 // f(lambda) = T, whose root is unique because f increases (Eq. 11).
 //
 // GPU procedure (one spectral pass per evaluation, no host round trip):
-//   each pass evaluates f at KNODES Chebyshev-Lobatto points of
-//   s = log(lambda) over the current bracket [lo, hi], accumulating the
-//   per-bin terms in FP32 per thread and in FP64 across warps and blocks;
-//   the last block of the image then either
-//     - interpolates f(s) through the nodes (barycentric form, FP64) and
-//       takes the root of the interpolant, when the bracket is narrow enough
-//       for the interpolant to be exact to ~1e-12 (f is analytic in the strip
-//       |Im s| < pi, its poles lying at lambda = -a_b), or
-//     - narrows the bracket to the sub-interval between the nodes that
-//       straddle T, or extends it past the end node when T is outside,
-//   and the next pass runs only for images whose root is still open.
+//   each pass evaluates f at KNODES nodes lambda_j of the current bracket,
+//   accumulating the per-bin terms in FP32 per thread and in FP64 across
+//   warps and blocks; one warp of the image's last block then updates the
+//   bracket.  Wide brackets use geometric nodes and are narrowed to the pair
+//   of nodes that straddles T.  Brackets of ratio <= 1.6 use Chebyshev-
+//   Lobatto nodes in lambda: f is analytic around such a bracket (its poles
+//   lie at lambda = -|H_b|^2 <= 0), so the degree-11 interpolant through the
+//   node values is exact to ~1e-12 relative, and its root is the answer.
+//   Node values are rounded to FP32 and used as the exact abscissae; the
+//   interpolant is evaluated in double-float arithmetic (FP64 is slow on
+//   this part), and its root is located by multisection with one trial
+//   point per lane, which needs only the sign of the interpolant.
 // The first pass of each iteration is fused into the forward column FFT and
-// is centred on the previous iteration's lambda.
+// uses the bracket [lambda_{k-1}/1.25, 1.25 lambda_{k-1}].
 #pragma once
 #include "common.cuh"
+#include "df.cuh"
 
 namespace gfd {
 
-constexpr double PI_D = 3.14159265358979323846;
-// log-width of a bracket over which the 12-node interpolant is trusted as
-// the final answer (ratio 4), and over which it is trusted as an estimate
-// that a +-2% bracket is placed around (ratio 64).
-constexpr double W_EXACT = 1.3862943611198906 * 1.000001;
-constexpr double W_ESTIMATE = 4.1588830833596715;
-constexpr double EST_HALF_WIDTH = 0.02;
-constexpr double PRIMARY_RATIO = 2.0;
-constexpr double INITIAL_LO = 1e-10, INITIAL_HI = 1e10;
+constexpr float INTERP_RATIO = 1.6f;   // largest bracket ratio interpolated
+constexpr float PRIMARY_RATIO = 1.25f;  // primary bracket: [lam/1.25, 1.25 lam]
+constexpr float INITIAL_LO = 1e-8f, INITIAL_HI = 1e4f;
+constexpr int MODE_GEOM = 0, MODE_CHEB = 1;
 
 // cos(pi j / (KNODES - 1)), j = 0..KNODES-1 (Chebyshev-Lobatto points)
-__device__ constexpr double kLobatto[KNODES] = {
-    1.0, 0.9594929736144974, 0.8412535328311812, 0.6548607339452851,
-    0.41541501300188644, 0.14231483827328512, -0.142314838273285, -0.4154150130018863,
-    -0.654860733945285, -0.8412535328311811, -0.9594929736144974, -1.0};
+__device__ constexpr float kLobatto[KNODES] = {
+    1.0f, 0.9594929736144974f, 0.8412535328311812f, 0.6548607339452851f,
+    0.41541501300188644f, 0.14231483827328512f, -0.142314838273285f, -0.4154150130018863f,
+    -0.654860733945285f, -0.8412535328311811f, -0.9594929736144974f, -1.0f};
 
-// Nodes of the next pass over [lo, hi], computed by the lanes of one warp
-// (lane j < KNODES owns node j).  The per-bin arithmetic uses the node
-// rounded to float; its exact logarithm (s + log1p(e), e the rounding's
-// relative error) is kept as the interpolation abscissa.
-GFD_D void set_bracket_warp(ImgState* st, double lo, double hi, int lane) {
+// Node lambda_j (ascending) of a bracket [lo, hi] for the given layout.
+GFD_D float bracket_node(float lo, float hi, int mode, int j) {
+  if (j == 0) return lo;
+  if (j == KNODES - 1) return hi;
+  if (mode == MODE_CHEB) {
+    const float c = 0.5f * (lo + hi), h = 0.5f * (hi - lo);
+    return c - h * kLobatto[j];
+  }
+  return lo * exp2f((float)j / (KNODES - 1) * log2f(hi / lo));
+}
+
+GFD_D int bracket_mode(float lo, float hi) { return hi <= INTERP_RATIO * lo ? MODE_CHEB : MODE_GEOM; }
+
+// Set the next pass's bracket (single thread).
+GFD_D void set_bracket(ImgState* st, float lo, float hi) {
+  const int mode = bracket_mode(lo, hi);
+  st->lo = lo;
+  st->hi = hi;
+  st->mode = mode;
+  for (int j = 0; j < KNODES; ++j) st->node[j] = bracket_node(lo, hi, mode, j);
+}
+
+// Warp variant: lane j < KNODES writes node j.
+GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane) {
+  const int mode = bracket_mode(lo, hi);
   if (lane == 0) {
     st->lo = lo;
     st->hi = hi;
+    st->mode = mode;
   }
-  if (lane < KNODES) {
-    const double a = log(lo), b = log(hi);
-    const double sj = 0.5 * (a + b) - 0.5 * (b - a) * kLobatto[lane];
-    const double e = exp(sj);
-    const float lf = (float)e;
-    const double rel = (double)lf / e - 1.0;
-    st->node[lane] = lf;
-    st->snode[lane] = sj + rel - 0.5 * rel * rel;
-  }
+  if (lane < KNODES) st->node[lane] = bracket_node(lo, hi, mode, lane);
   __syncwarp();
-}
-
-// Single-thread variant for the setup kernel.
-GFD_D void set_bracket(ImgState* st, double lo, double hi) {
-  st->lo = lo;
-  st->hi = hi;
-  const double a = log(lo), b = log(hi);
-  for (int j = 0; j < KNODES; ++j) {
-    const double sj = 0.5 * (a + b) - 0.5 * (b - a) * kLobatto[j];
-    const double e = exp(sj);
-    const float lf = (float)e;
-    const double rel = (double)lf / e - 1.0;
-    st->node[j] = lf;
-    st->snode[j] = sj + rel - 0.5 * rel * rel;
-  }
 }
 
 // One bin's contribution: wr = (Hermitian weight) * r, a = |H|^2.
@@ -154,62 +149,60 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
   return last;
 }
 
-GFD_D double warp_sum_full(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// 1/d in FP64 from an FP32 seed and two Newton steps (|d| within FP32 range).
-GFD_D double rcp_d(double d) {
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
-// Root in s of the interpolant of (s_m, f_m) minus T inside [s_j, s_{j+1}]
-// (f increases through T there), as lambda = exp(s).  Lane m < KNODES holds
-// node m; the barycentric sums are warp reductions.  Safeguarded Newton:
-// steps leaving the bracket fall back to bisection.
-GFD_D double interp_root_warp(double sm, double fm, double T, int j, int lane) {
+// Root of the interpolant through (x_m, g_m), m < KNODES (x ascending FP32
+// values used as exact abscissae, g increasing through 0 between x_j and
+// x_{j+1}).  Lane m < KNODES holds (x_m, g_m).  Barycentric weights and the
+// interpolant are formed in double-float; the root is bracketed by
+// multisection: every lane evaluates the sign of the interpolant at its own
+// trial point, and the bracket shrinks 33-fold per round.  Returns lambda.
+GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
   const bool own = lane < KNODES;
-  double prod = 1.0;
+  // weight w_m = 1 / prod_{n != m} (x_m - x_n); the differences are exact
+  // (Sterbenz: the nodes lie within a factor 1.6 of each other)
+  df prod = df_make(1.0f);
   for (int n = 0; n < KNODES; ++n) {
-    const double sn = __shfl_sync(0xffffffffu, sm, n);
-    if (n != lane) prod *= (sm - sn);
+    const float xn = __shfl_sync(0xffffffffu, xm, n);
+    if (own && n != lane) prod = df_mul_f(prod, xm - xn);
   }
-  const double wb = own ? 1.0 / prod : 0.0;
-  double a = __shfl_sync(0xffffffffu, sm, j), b = __shfl_sync(0xffffffffu, sm, j + 1);
-  const double fa = __shfl_sync(0xffffffffu, fm, j) - T;
-  const double fb = __shfl_sync(0xffffffffu, fm, j + 1) - T;
-  if (fa == 0.0) return exp(a);
-  if (fb == 0.0) return exp(b);
-  double x = a - fa * (b - a) / (fb - fa);
-  if (!(x > a && x < b)) x = 0.5 * (a + b);
-  for (int it = 0; it < 40; ++it) {
-    const double d = x - sm;
-    const unsigned hit = __ballot_sync(0xffffffffu, own && d == 0.0);
-    if (hit) return exp(x);  // x is a node; bracket ends already excluded roots there
-    const double rd = own ? rcp_d(d) : 0.0;
-    const double t = wb * rd;
-    const double N = warp_sum_full(t * fm);
-    const double D = warp_sum_full(t);
-    const double r = N / D;
-    const double dr = warp_sum_full(own ? t * (r - fm) * rd : 0.0) / D;
-    const double g = r - T;
-    if (g < 0.0)
-      a = x;
-    else
-      b = x;
-    double xn = x - g / dr;
-    if (!(xn > a && xn < b)) xn = 0.5 * (a + b);
-    const double step = fabs(xn - x);
-    x = xn;
-    if (step <= 1e-15 * fmax(1.0, fabs(x)) || b - a <= 1e-15 * fmax(1.0, fabs(a))) break;
+  const df w = own ? df_rcp(prod) : df_make(0.0f);
+  __shared__ float s_x[KNODES], s_g[KNODES];
+  __shared__ df s_w[KNODES];
+  if (own) {
+    s_x[lane] = xm;
+    s_g[lane] = gm;
+    s_w[lane] = w;
   }
-  return exp(x);
+  __syncwarp();
+  df a = df_make(s_x[j]), b = df_make(s_x[j + 1]);
+  for (int round = 0; round < 7; ++round) {
+    // trial point a + (b - a) (lane + 1) / 33
+    const df width = df_sub(b, a);
+    const df t = df_add(a, df_mul_f(width, (float)(lane + 1) / 33.0f));
+    df num = df_make(0.0f), den = df_make(0.0f);
+    bool at_node = false;
+    float node_g = 0.0f;
+    for (int m = 0; m < KNODES; ++m) {
+      const df d = df_sub(t, df_make(s_x[m]));
+      if (d.hi == 0.0f) {
+        at_node = true;
+        node_g = s_g[m];
+        continue;
+      }
+      const df q = df_mul(s_w[m], df_rcp(d));
+      num = df_add(num, df_mul_f(q, s_g[m]));
+      den = df_add(den, q);
+    }
+    const bool neg = at_node ? (node_g < 0.0f) : ((num.hi < 0.0f) != (den.hi < 0.0f));
+    const unsigned below = __ballot_sync(0xffffffffu, neg);
+    // the interpolant increases: trial points below the root form a prefix
+    const int nb = __popc(below);  // lanes 0..nb-1 are below the root
+    const df na = nb > 0 ? df_add(a, df_mul_f(width, (float)nb / 33.0f)) : a;
+    const df nbv = nb < 32 ? df_add(a, df_mul_f(width, (float)(nb + 1) / 33.0f)) : b;
+    a = na;
+    b = nbv;
+    if (df_to_double(df_sub(b, a)) <= 1e-12 * (double)s_x[j]) break;
+  }
+  return 0.5 * (df_to_double(a) + df_to_double(b));
 }
 
 GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int lane) {
@@ -218,18 +211,22 @@ GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int
     st->need = 0;
     if (lam_out) lam_out[iter] = lam;
   }
-  if (isfinite(lam) && lam > 0.0) set_bracket_warp(st, lam / PRIMARY_RATIO, lam * PRIMARY_RATIO, lane);
+  if (isfinite(lam) && lam > 0.0)
+    set_bracket_warp(st, (float)(lam / PRIMARY_RATIO), (float)(lam * PRIMARY_RATIO), lane);
+  __syncwarp();
 }
 
 // Consume the totals of the pass that just completed for this image (tot:
 // KNODES node sums and the residual sum, visible to the warp).  Run by the
 // 32 lanes of one warp of the image's last block; every lane takes the same
-// decisions from the same values.
+// decisions from the same values.  FP64 is limited to a handful of
+// operations (the sums themselves are FP64).
 GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool primary,
                               bool last_chance, int iter, double* lam_out, double* res_out,
                               int lane) {
+  const double invP = 1.0 / P;  // P is a power of two: exact
   const double T = st->T;
-  const double resinf = tot[KNODES] / P;
+  const double resinf = tot[KNODES] * invP;
   if (primary) {
     if (lane == 0) {
       st->res = resinf;
@@ -244,44 +241,46 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
       resolve_warp(st, INFINITY, iter, lam_out, lane);
       return;
     }
-    const double t = sqrt(T / resinf);
-    if (lane == 0) st->lam_up = fmin(1e30, st->amax * t / (1.0 - t));
+    if (lane == 0) {
+      const float t = sqrtf((float)T / (float)resinf);
+      st->lam_up = fminf(1e30f, (float)st->amax * t / (1.0f - t));
+    }
     __syncwarp();
   }
-  const double f0 = tot[0] / P, fK = tot[KNODES - 1] / P;
-  const double lo = (double)st->node[0], hi = (double)st->node[KNODES - 1];
+  // g_m = f(lambda_m) / T - 1, increasing in lambda
+  const float gm = lane < KNODES ? (float)((tot[lane] * invP - T) * st->invT) : 0.0f;
+  const float xm = lane < KNODES ? st->node[lane] : 0.0f;
+  const float g0 = __shfl_sync(0xffffffffu, gm, 0);
+  const float gK = __shfl_sync(0xffffffffu, gm, KNODES - 1);
+  const float lo = __shfl_sync(0xffffffffu, xm, 0);
+  const float hi = __shfl_sync(0xffffffffu, xm, KNODES - 1);
+  const int mode = st->mode;
   bool open = true;
-  if (!(f0 <= T)) {  // root below the bracket (or NaN)
-    if (!isfinite(f0)) {
+  if (!(g0 <= 0.0f)) {  // root below the bracket (or NaN)
+    if (!isfinite(g0)) {
       if (lane == 0) st->status |= ST_NONFINITE;
       resolve_warp(st, INFINITY, iter, lam_out, lane);
       return;
     }
-    if (lo <= LAMBDA_LO * 1.000001) {
+    if (lo <= (float)LAMBDA_LO * 1.000001f) {
       if (lane == 0) st->status |= ST_NONCONVERGED;
       resolve_warp(st, LAMBDA_LO, iter, lam_out, lane);
       return;
     }
-    set_bracket_warp(st, LAMBDA_LO, lo, lane);
-  } else if (fK < T) {  // root above the bracket
-    set_bracket_warp(st, hi, fmax(st->lam_up, hi * 4.0), lane);
+    set_bracket_warp(st, (float)LAMBDA_LO, lo, lane);
+  } else if (gK < 0.0f) {  // root above the bracket
+    set_bracket_warp(st, hi, fmaxf(st->lam_up, hi * 4.0f), lane);
   } else {
-    int j = 0;
-    while (j < KNODES - 2 && tot[j + 1] / P < T) ++j;
-    const double sm = lane < KNODES ? st->snode[lane] : 0.0;
-    const double fm = lane < KNODES ? tot[lane] / P : 0.0;
-    const double W = st->snode[KNODES - 1] - st->snode[0];
-    if (W <= W_EXACT) {
-      const double lam = interp_root_warp(sm, fm, T, j, lane);
+    // nodes with g < 0 form a prefix 0..j
+    const unsigned below = __ballot_sync(0xffffffffu, lane < KNODES && gm < 0.0f);
+    int j = 31 - __clz(below | 1u);
+    if (j > KNODES - 2) j = KNODES - 2;
+    if (mode == MODE_CHEB) {
+      const double lam = interp_root_warp(xm, gm, j, lane);
       resolve_warp(st, lam, iter, lam_out, lane);
       open = false;
-    } else if (W <= W_ESTIMATE) {
-      const double est = interp_root_warp(sm, fm, T, j, lane);
-      __syncwarp();
-      set_bracket_warp(st, est * (1.0 - EST_HALF_WIDTH), est * (1.0 + EST_HALF_WIDTH), lane);
     } else {
-      const double nlo = (double)st->node[j], nhi = (double)st->node[j + 1];
-      __syncwarp();
+      const float nlo = __shfl_sync(0xffffffffu, xm, j), nhi = __shfl_sync(0xffffffffu, xm, j + 1);
       set_bracket_warp(st, nlo, nhi, lane);
     }
   }
@@ -289,7 +288,7 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
     if (lane == 0) st->need = 1;
     if (last_chance) {
       if (lane == 0) st->status |= ST_NONCONVERGED;
-      const double mid = sqrt(st->lo * st->hi);
+      const double mid = sqrt((double)st->lo * (double)st->hi);
       __syncwarp();
       resolve_warp(st, mid, iter, lam_out, lane);
     }
