@@ -274,7 +274,10 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
 // the first evaluation of Eq. 11 at the nodes of the image's bracket.  The S,
 // H and Y tiles of the next item land while the current one is processed
-// (S only for M = 4096, where three landing tiles do not fit).
+// (S only for M = 4096, where three landing tiles do not fit).  A block
+// takes a contiguous range of items and keeps its per-node sums in registers
+// while consecutive items belong to the same image; it publishes them (one
+// partial slot, one counter update) only when the image changes.
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
@@ -289,6 +292,9 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
   const int n_items = cd.n_img * cpi;
+  const int per_cta = (n_items + gridDim.x - 1) / gridDim.x;
+  const int first = blockIdx.x * per_cta;
+  const int stop = min(first + per_cta, n_items);
   const int tile = M * B;
   float2* landS = smem;
   float2* landH = landS + tile;
@@ -297,7 +303,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   double* red = reinterpret_cast<double*>(work + B * team_stride(M));
   const int b = threadIdx.x % B, j = threadIdx.x / B;
   auto issue = [&](int item) {
-    if (item < n_items) {
+    if (item < stop) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
       issue_tile(landS, d.S + off, M, B, B);
@@ -308,17 +314,56 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     }
     cp_async_commit();
   };
-  issue(blockIdx.x);
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  float acc[KNODES + 1];
+#pragma unroll
+  for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
+  int cur = -1, slot = 0, count = 0;
+  // publish the sums of `count` items of image `cur` (slot = its first tile);
+  // the block completing the image's count reduces all slots and updates
+  // the image's lambda
+  auto flush = [&]() {
+    ImgState* S = st + cur;
+    const ImgDesc& d = imgs[cur];
+    block_partials(acc, red, d.part + (size_t)slot * (KNODES + 1));
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int prev = atomicAdd(&S->cta_done, (unsigned int)count);
+      s_flag = (prev + count == (unsigned int)cpi);
+    }
+    __syncthreads();
+    if (s_flag) {
+      __threadfence();
+      block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
+      for (int q = threadIdx.x; q < cpi * (KNODES + 1); q += blockDim.x) d.part[q] = 0.0;
+      if (threadIdx.x < 32)
+        lambda_update_warp(S, s_tot, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out,
+                           threadIdx.x);
+      if (threadIdx.x == 0) {
+        S->cta_done = 0;
+        __threadfence();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
+    count = 0;
+  };
+  issue(first);
+  for (int item = first; item < stop; ++item) {
     cp_async_wait<0>();
     __syncthreads();
     const int gi = cd.img0 + item / cpi;
+    const int t = item % cpi;
+    if (gi != cur) {
+      if (count > 0) flush();
+      cur = gi;
+      slot = t;
+      for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&st[gi].node[q]);
+    }
     const ImgDesc& d = imgs[gi];
     ImgState* S = st + gi;
-    const int t = item % cpi;
     const int col = t * B + b;
     const size_t off = (size_t)t * tile;
-    for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
     if (t == 0) {  // the DC bin needs sum(u_E): total of the row pass's partials
       block_sum_columns(d.rowsum, row_items, 1, 1, red, s_tot);
       if (threadIdx.x == 0) S->sum_u = s_tot[0];
@@ -328,9 +373,6 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     float nodes[KNODES];
 #pragma unroll
     for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
-    float acc[KNODES + 1];
-#pragma unroll
-    for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
     float2* spec = d.S + off + b;
     if (col != 0) {
 #pragma unroll 4
@@ -377,19 +419,11 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         spec[(size_t)k * B] = U;
       }
     }
-    block_partials(acc, red, d.part + (size_t)t * (KNODES + 1));  // ends synchronised
-    issue(item + gridDim.x);  // every landing tile of this item is consumed
-    if (last_item(&S->cta_done, cpi, &s_flag)) {
-      block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
-      if (threadIdx.x < 32)
-        lambda_update_warp(S, s_tot, (double)cd.M * cd.N, true, false, iter, d.lam_out, d.res_out,
-                           threadIdx.x);
-      if (threadIdx.x == 0) {
-        S->cta_done = 0;
-        __threadfence();
-      }
-    }
+    ++count;
+    __syncthreads();      // every landing tile of this item is consumed
+    issue(item + 1);
   }
+  if (count > 0) flush();
   cp_async_wait<0>();
 }
 
@@ -450,6 +484,7 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
   block_partials(acc, red, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
   if (last_item(&S->cta_done, cpi, &s_flag)) {
     block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
+    for (int q = threadIdx.x; q < cpi * (KNODES + 1); q += blockDim.x) d.part[q] = 0.0;
     if (threadIdx.x < 32)
       lambda_update_warp(S, s_tot, (double)cd.M * cd.N, false, last_chance != 0, iter,
                          d.lam_out, d.res_out, threadIdx.x);

@@ -98,6 +98,14 @@ __global__ void k_setup_init(ClassDesc cd, const ImgDesc* __restrict__ imgs, Img
   set_bracket(S, INITIAL_LO, INITIAL_HI);
 }
 
+// Zero the per-item partial slots of the spectral passes (each pass leaves
+// them zeroed again after reducing them).
+__global__ void k_zero_parts(ClassDesc cd, const ImgDesc* __restrict__ imgs, int n_slots) {
+  const ImgDesc& d = imgs[cd.img0 + blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x)
+    d.part[i] = 0.0;
+}
+
 // Circular PSF embedding: offset (a - kh/2, b - kw/2) -> canvas index mod (M, N).
 __global__ void k_embed_psf(ClassDesc cd, const ImgDesc* __restrict__ imgs, int dst_sel) {
   const size_t P = (size_t)cd.M * cd.N;
@@ -163,6 +171,10 @@ cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
 
 cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s) {
   k_setup_init<<<(c.cd.n_img + 127) / 128, 128, 0, s>>>(c.cd, c.imgs, c.st, rho_fixed);
+  const size_t Lc = c.cd.N / 2;
+  const size_t col_items = Lc / 2, pass_items = (size_t)c.cd.M * Lc / 4096 + 1;
+  const int n_slots = (int)((KNODES + 1) * (col_items > pass_items ? col_items : pass_items));
+  k_zero_parts<<<dim3((n_slots + 255) / 256, c.cd.n_img), 256, 0, s>>>(c.cd, c.imgs, n_slots);
   return cudaGetLastError();
 }
 

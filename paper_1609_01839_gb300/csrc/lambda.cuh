@@ -157,12 +157,20 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
 // trial point, and the bracket shrinks 33-fold per round.  Returns lambda.
 GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
   const bool own = lane < KNODES;
+  // All abscissa differences are scaled by a power of two ~ 1/(bracket
+  // width): exact, and it keeps the products of 11 differences in FP32
+  // range (the barycentric ratio does not depend on the scale).
+  const float x0 = __shfl_sync(0xffffffffu, xm, 0);
+  const float xK = __shfl_sync(0xffffffffu, xm, KNODES - 1);
+  int ex;
+  frexpf(xK - x0, &ex);
+  const float sc = ldexpf(1.0f, -ex);
   // weight w_m = 1 / prod_{n != m} (x_m - x_n); the differences are exact
   // (Sterbenz: the nodes lie within a factor 1.6 of each other)
   df prod = df_make(1.0f);
   for (int n = 0; n < KNODES; ++n) {
     const float xn = __shfl_sync(0xffffffffu, xm, n);
-    if (own && n != lane) prod = df_mul_f(prod, xm - xn);
+    if (own && n != lane) prod = df_mul_f(prod, (xm - xn) * sc);
   }
   const df w = own ? df_rcp(prod) : df_make(0.0f);
   __shared__ float s_x[KNODES], s_g[KNODES];
@@ -182,12 +190,13 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
     bool at_node = false;
     float node_g = 0.0f;
     for (int m = 0; m < KNODES; ++m) {
-      const df d = df_sub(t, df_make(s_x[m]));
-      if (d.hi == 0.0f) {
+      const df dd = df_sub(t, df_make(s_x[m]));
+      if (dd.hi == 0.0f) {
         at_node = true;
         node_g = s_g[m];
         continue;
       }
+      const df d{dd.hi * sc, dd.lo * sc};
       const df q = df_mul(s_w[m], df_rcp(d));
       num = df_add(num, df_mul_f(q, s_g[m]));
       den = df_add(den, q);
