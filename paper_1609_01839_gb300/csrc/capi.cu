@@ -216,7 +216,15 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
     cl.imgs = c->d_imgs;
     cl.st = c->d_st;
     cl.max_rad = 0;
+    cl.n_rad_groups = 0;
+    // order the class by window radius: one guided-filter launch per radius
+    std::stable_sort(members[ci].begin(), members[ci].end(),
+                     [&](int a, int b) { return imgs[a].w < imgs[b].w; });
     for (int ui : members[ci]) {
+      const int rad = (imgs[ui].w - 1) / 2;
+      if (cl.n_rad_groups == 0 || cl.rad_groups[cl.n_rad_groups - 1].rad != rad)
+        cl.rad_groups[cl.n_rad_groups++] = RadGroup{(int)pl.order.size(), 0, rad};
+      cl.rad_groups[cl.n_rad_groups - 1].n_img += 1;
       const gfdeconv_image& im = imgs[ui];
       const size_t P = (size_t)im.M * im.N;
       ImgDesc d{};
@@ -690,6 +698,8 @@ int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, 
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
   cl.max_rad = (w - 1) / 2;
+  cl.n_rad_groups = 1;
+  cl.rad_groups[0] = RadGroup{0, 1, (w - 1) / 2};
   if ((e = launch_guided_filter(cl, -1, c->opts.var_precision == 1 ? 1 : 0, s)) != cudaSuccess)
     return map_err(e);
   return map_err(aux_finish(a, s));

@@ -1,262 +1,344 @@
-// Guided filter u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5), periodic
-// windows, one 32 x 32 output tile per block.
+// Guided filter u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5) with
+// periodic windows, streamed down column strips.
 //
-// With r = (w-1)/2 the block loads the (32+4r)^2 input tile (periodic wrap),
-// forms the window sums of I, p, I*I and I*p over the (32+2r)^2 pixels whose
-// coefficients the tile needs (separable: column sums, then row sums, each a
-// sliding window), computes a_k (Eq. 3) and b_k (Eq. 4) there, and then the
-// window means of a and b over the tile to give u = abar I + bbar (Eq. 5).
-// The cost per pixel does not depend on w (the O(N^2) exact box filter the
-// paper relies on).
-//
-// Window statistics are taken about a per-tile reference value (the guidance
-// and input at the tile centre): sigma_k^2 = E[(I-c)^2] - (E[I]-c)^2 is the
-// same number as E[I^2] - mu^2 but without its cancellation where the window
-// mean is close to c.
+// A work item is a strip of W output columns and H output rows of one image.
+// With r = (w-1)/2 the block streams the H + 4r input rows of the strip's
+// W + 4r input columns (periodic wrap) through a ring buffer in shared
+// memory, GF_RB rows per batch, the next batch being copied asynchronously
+// while the current one is processed:
+//   1. window sums down each column of I-c_I, p-c_p, their squares and
+//      product (running sums, Kahan-compensated);
+//   2. window sums along each row of those -> mu_k, pbar_k, sigma_k^2 and
+//      the covariance -> a_k (Eq. 3), b_k (Eq. 4), into a ring of (a, b) rows;
+//   3. running window sums of a and b down each column (compensated);
+//   4. window sums along each row -> abar, bbar -> u = abar I + bbar (Eq. 5).
+// Every sum costs O(1) per pixel, independent of w (the O(N^2) exact box
+// filter the paper relies on).  Window statistics are taken about reference
+// values (c_I, c_p: the item's centre pixel), which removes the cancellation
+// in sigma_k^2 = E[I^2] - mu^2 where the window mean is close to c_I.
 #include "common.cuh"
 #include "launch.h"
 
 namespace gfd {
 
-constexpr int GF_T = 32;        // tile edge
+constexpr int GF_W = 128;      // output columns per item (at most N)
+constexpr int GF_H = 128;      // output rows per item (at most M)
+constexpr int GF_RB = 8;       // input rows per batch
+constexpr int GF_C = 4;        // columns per thread in the row sums
 constexpr int GF_THREADS = 256;
-constexpr int GF_SEG = 8;       // sliding run length
-constexpr int GF_RMAX = 8;      // w <= 17
+constexpr int GF_RMAX = 8;     // w <= 17
 
-GFD_HD int gf_pitch(int w) { return w | 1; }
+GFD_HD int gf_rin(int rad) { return 2 * GF_RB + 2 * rad + 1; }
+GFD_HD int gf_rab(int rad) { return GF_RB + 2 * rad + 1; }
 GFD_HD size_t gf_smem_floats(int rad) {
-  const int H0 = GF_T + 4 * rad, W0 = H0, H1 = GF_T + 2 * rad, W1 = H1;
-  const int P0 = gf_pitch(W0), P1 = gf_pitch(W1);
-  return (size_t)2 * H0 * P0 + (size_t)4 * H1 * P0 + (size_t)2 * H1 * P1;
+  const int Win = GF_W + 4 * rad, W1 = GF_W + 2 * rad;
+  return (size_t)gf_rin(rad) * 2 * Win + (size_t)GF_RB * 4 * Win + (size_t)gf_rab(rad) * 2 * W1 +
+         (size_t)GF_RB * 2 * W1;
+}
+
+struct Kahan {
+  float s, c;
+};
+GFD_D void kadd(Kahan& k, float x) {
+  const float y = x - k.c;
+  const float t = k.s + y;
+  k.c = (t - k.s) - y;
+  k.s = t;
+}
+GFD_D float kval(const Kahan& k) { return k.s - k.c; }
+
+GFD_D void cp_async4(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+               : "memory");
 }
 
 template <int RAD>
-GFD_D void gf_tile(const float* __restrict__ I, const float* __restrict__ p, float* __restrict__ u,
-                   const float* __restrict__ uo, int M, int N, int y0, int x0, float eps,
-                   bool shifted, float* sm, float& err) {
-  constexpr int WIN = 2 * RAD + 1;
-  constexpr int H0 = GF_T + 4 * RAD, W0 = H0, H1 = GF_T + 2 * RAD, W1 = H1;
-  constexpr int P0 = W0 | 1, P1 = W1 | 1;
-  float* sI = sm;
-  float* sP = sI + H0 * P0;
-  float* vJ = sP + H0 * P0;
-  float* vQ = vJ + H1 * P0;
-  float* vJJ = vQ + H1 * P0;
-  float* vJQ = vJJ + H1 * P0;
-  float* sA = vJQ + H1 * P0;
-  float* sB = sA + H1 * P1;
-  float* va = vJJ;  // stage-2 column sums reuse dead stage-1 storage
-  float* vb = vJQ;
-  float* so = sA;   // output tile reuses sA after stage 2's column sums
+struct GfLayout {
+  static constexpr int WIN = 2 * RAD + 1;
+  static constexpr int Win = GF_W + 4 * RAD;  // input columns
+  static constexpr int W1 = GF_W + 2 * RAD;   // columns of a, b
+  static constexpr int Rin = 2 * GF_RB + 2 * RAD + 1;
+  static constexpr int Rab = GF_RB + 2 * RAD + 1;
+  float* in;   // [Rin][2][Win]   input rows (I, p)
+  float* vs;   // [RB][4][Win]    column window sums of the batch rows
+  float* ab;   // [Rab][2][W1]    a, b rows
+  float* vs2;  // [RB][2][W1]     column window sums of a, b
+  GFD_D explicit GfLayout(float* sm) {
+    in = sm;
+    vs = in + Rin * 2 * Win;
+    ab = vs + GF_RB * 4 * Win;
+    vs2 = ab + Rab * 2 * W1;
+  }
+};
+
+template <int RAD>
+GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
+                    bool shifted, int W, int H, float* sm, double* red, int* s_flag) {
+  using Lay = GfLayout<RAD>;
+  constexpr int WIN = Lay::WIN, Win = Lay::Win, W1 = Lay::W1, Rin = Lay::Rin, Rab = Lay::Rab;
+  const Lay L(sm);
+  const int M = cd.M, N = cd.N;
   const int tid = threadIdx.x;
+  const int strips = N / W, blocks = M / H;
+  const int per_img = strips * blocks;
+  const int n_items = cd.n_img * per_img;
+  const int nrows = H + 4 * RAD;  // input rows of an item
+  const int nq = (nrows + GF_RB - 1) / GF_RB;
+  const int win_used = W + 4 * RAD, w1_used = W + 2 * RAD;
   const float inv_n = 1.0f / (float)(WIN * WIN);
 
-  float cI = 0.0f, cP = 0.0f;
-  if (shifted) {
-    const size_t c = (size_t)((y0 + GF_T / 2) & (M - 1)) * N + ((x0 + GF_T / 2) & (N - 1));
-    cI = __ldg(&I[c]);
-    cP = __ldg(&p[c]);
-  }
-  for (int idx = tid; idx < H0 * W0; idx += GF_THREADS) {
-    const int ty = idx / W0, tx = idx - ty * W0;
-    const size_t g = (size_t)((y0 - 2 * RAD + ty) & (M - 1)) * N + ((x0 - 2 * RAD + tx) & (N - 1));
-    sI[ty * P0 + tx] = __ldg(&I[g]);
-    sP[ty * P0 + tx] = __ldg(&p[g]);
-  }
-  __syncthreads();
-
-  // stage 1, column sums of J = I - cI, Q = p - cP, J*J, J*Q over WIN rows
-  constexpr int NS1 = (H1 + GF_SEG - 1) / GF_SEG;
-  for (int item = tid; item < W0 * NS1; item += GF_THREADS) {
-    const int x = item % W0, sg = item / W0;
-    const int oy0 = sg * GF_SEG;
-    const int oy1 = min(oy0 + GF_SEG, H1);
-    float sj = 0.f, sq = 0.f, sjj = 0.f, sjq = 0.f;
-#pragma unroll
-    for (int dd = 0; dd < WIN; ++dd) {
-      const float J = sI[(oy0 + dd) * P0 + x] - cI, Q = sP[(oy0 + dd) * P0 + x] - cP;
-      sj += J;
-      sq += Q;
-      sjj = fmaf(J, J, sjj);
-      sjq = fmaf(J, Q, sjq);
-    }
-    vJ[oy0 * P0 + x] = sj;
-    vQ[oy0 * P0 + x] = sq;
-    vJJ[oy0 * P0 + x] = sjj;
-    vJQ[oy0 * P0 + x] = sjq;
-    for (int oy = oy0 + 1; oy < oy1; ++oy) {
-      const float Jn = sI[(oy + 2 * RAD) * P0 + x] - cI, Qn = sP[(oy + 2 * RAD) * P0 + x] - cP;
-      const float Jo = sI[(oy - 1) * P0 + x] - cI, Qo = sP[(oy - 1) * P0 + x] - cP;
-      sj += Jn - Jo;
-      sq += Qn - Qo;
-      sjj += fmaf(Jn, Jn, -Jo * Jo);
-      sjq += fmaf(Jn, Qn, -Jo * Qo);
-      vJ[oy * P0 + x] = sj;
-      vQ[oy * P0 + x] = sq;
-      vJJ[oy * P0 + x] = sjj;
-      vJQ[oy * P0 + x] = sjq;
-    }
-  }
-  __syncthreads();
-
-  // stage 1, row sums -> a_k (Eq. 3), b_k (Eq. 4)
-  constexpr int NSW1 = (W1 + GF_SEG - 1) / GF_SEG;
-  for (int item = tid; item < H1 * NSW1; item += GF_THREADS) {
-    const int oy = item % H1, sg = item / H1;
-    const int ox0 = sg * GF_SEG;
-    const int ox1 = min(ox0 + GF_SEG, W1);
-    const float* rJ = vJ + oy * P0;
-    const float* rQ = vQ + oy * P0;
-    const float* rJJ = vJJ + oy * P0;
-    const float* rJQ = vJQ + oy * P0;
-    float sj = 0.f, sq = 0.f, sjj = 0.f, sjq = 0.f;
-#pragma unroll
-    for (int dd = 0; dd < WIN; ++dd) {
-      sj += rJ[ox0 + dd];
-      sq += rQ[ox0 + dd];
-      sjj += rJJ[ox0 + dd];
-      sjq += rJQ[ox0 + dd];
-    }
-    for (int ox = ox0; ox < ox1; ++ox) {
-      if (ox > ox0) {
-        sj += rJ[ox + 2 * RAD] - rJ[ox - 1];
-        sq += rQ[ox + 2 * RAD] - rQ[ox - 1];
-        sjj += rJJ[ox + 2 * RAD] - rJJ[ox - 1];
-        sjq += rJQ[ox + 2 * RAD] - rJQ[ox - 1];
-      }
-      const float mJ = sj * inv_n, mQ = sq * inv_n;
-      const float var = fmaf(-mJ, mJ, sjj * inv_n);   // sigma_k^2
-      const float cov = fmaf(-mJ, mQ, sjq * inv_n);   // mean(I p) - mu pbar
-      const float a = cov / (var + eps);
-      const float b = (mQ + cP) - a * (mJ + cI);
-      sA[oy * P1 + ox] = a;
-      sB[oy * P1 + ox] = b;
-    }
-  }
-  __syncthreads();
-
-  // stage 2, column sums of a and b over WIN rows
-  constexpr int NS2 = (GF_T + GF_SEG - 1) / GF_SEG;
-  for (int item = tid; item < W1 * NS2; item += GF_THREADS) {
-    const int x = item % W1, sg = item / W1;
-    const int oy0 = sg * GF_SEG;
-    const int oy1 = min(oy0 + GF_SEG, GF_T);
-    float s_a = 0.f, s_b = 0.f;
-#pragma unroll
-    for (int dd = 0; dd < WIN; ++dd) {
-      s_a += sA[(oy0 + dd) * P1 + x];
-      s_b += sB[(oy0 + dd) * P1 + x];
-    }
-    va[oy0 * P1 + x] = s_a;
-    vb[oy0 * P1 + x] = s_b;
-    for (int oy = oy0 + 1; oy < oy1; ++oy) {
-      s_a += sA[(oy + 2 * RAD) * P1 + x] - sA[(oy - 1) * P1 + x];
-      s_b += sB[(oy + 2 * RAD) * P1 + x] - sB[(oy - 1) * P1 + x];
-      va[oy * P1 + x] = s_a;
-      vb[oy * P1 + x] = s_b;
-    }
-  }
-  __syncthreads();
-
-  // stage 2, row sums -> u = abar I + bbar (Eq. 5)
-  constexpr int NSW2 = (GF_T + GF_SEG - 1) / GF_SEG;
-  for (int item = tid; item < GF_T * NSW2; item += GF_THREADS) {
-    const int ty = item % GF_T, sg = item / GF_T;
-    const int tx0 = sg * GF_SEG;
-    const float* ra = va + ty * P1;
-    const float* rb = vb + ty * P1;
-    float s_a = 0.f, s_b = 0.f;
-#pragma unroll
-    for (int dd = 0; dd < WIN; ++dd) {
-      s_a += ra[tx0 + dd];
-      s_b += rb[tx0 + dd];
-    }
-    for (int tx = tx0; tx < tx0 + GF_SEG; ++tx) {
-      if (tx > tx0) {
-        s_a += ra[tx + 2 * RAD] - ra[tx - 1];
-        s_b += rb[tx + 2 * RAD] - rb[tx - 1];
-      }
-      const float Iv = sI[(ty + 2 * RAD) * P0 + tx + 2 * RAD];
-      so[ty * GF_T + tx] = fmaf(s_a * inv_n, Iv, s_b * inv_n);
-    }
-  }
-  __syncthreads();
-  for (int idx = tid; idx < GF_T * GF_T; idx += GF_THREADS) {
-    const int ty = idx / GF_T, tx = idx - ty * GF_T;
-    const int gy = y0 + ty, gx = x0 + tx;
-    if (gy < M && gx < N) {
-      const float v = so[idx];
-      u[(size_t)gy * N + gx] = v;
-      if (uo) {
-        const float e = v - __ldg(&uo[(size_t)gy * N + gx]);
-        err = fmaf(e, e, err);
+  // Input row y of an item whose row 0 has stream index `base` lives in ring
+  // slot (base + y) % Rin; consecutive items continue the stream, so the next
+  // item's first batch can be fetched during the current item's last one.
+  auto prefetch = [&](int item, int q, int base) {
+    if (item < n_items) {
+      const int li = item / per_img, rem = item - li * per_img;
+      const int y0 = (rem / strips) * H, x0 = (rem % strips) * W;
+      const ImgDesc& d = imgs[cd.img0 + li];
+      const int r0 = q * GF_RB;
+      const int rows = min(GF_RB, nrows - r0);
+      for (int e = tid; e < 2 * rows * win_used; e += blockDim.x) {
+        const int plane = e / (rows * win_used);
+        const int rr = e - plane * rows * win_used;
+        const int row = rr / win_used, c = rr - row * win_used;
+        const int gy = (y0 - 2 * RAD + r0 + row) & (M - 1);
+        const int gx = (x0 - 2 * RAD + c) & (N - 1);
+        const float* src = (plane == 0 ? d.uI : d.up) + (size_t)gy * N + gx;
+        cp_async4(L.in + ((base + r0 + row) % Rin) * 2 * Win + plane * Win + c, src);
       }
     }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  int base = 0;  // stream index of the current item's input row 0
+  prefetch(item, 0, base);
+  while (item < n_items) {
+    const int li = item / per_img, rem = item - li * per_img;
+    const int y0 = (rem / strips) * H, x0 = (rem % strips) * W;
+    const int gi = cd.img0 + li;
+    const ImgDesc& d = imgs[gi];
+    const float* uo = (iter >= 0 && d.isnr_out) ? d.uo : nullptr;
+    float cI = 0.0f, cP = 0.0f;
+    if (shifted) {
+      const size_t c = (size_t)((y0 + H / 2) & (M - 1)) * N + ((x0 + W / 2) & (N - 1));
+      cI = __ldg(&d.uI[c]);
+      cP = __ldg(&d.up[c]);
+    }
+    const float eps = (float)d.eps;
+    Kahan sJ{0, 0}, sQ{0, 0}, sJJ{0, 0}, sJQ{0, 0}, sa{0, 0}, sb{0, 0};
+    float err = 0.0f;
+    const int next_base = base + nq * GF_RB;
+    for (int q = 0; q < nq; ++q) {
+      cp_async_wait<0>();
+      __syncthreads();
+      if (q + 1 < nq)
+        prefetch(item, q + 1, base);
+      else
+        prefetch(item + gridDim.x, 0, next_base);
+      const int r0 = q * GF_RB;
+      const int rows = min(GF_RB, nrows - r0);
+      // 1. column window sums of the four statistics (input column tid)
+      if (tid < win_used) {
+        for (int rho = 0; rho < rows; ++rho) {
+          const int y = r0 + rho;
+          const float* rn = L.in + ((base + y) % Rin) * 2 * Win;
+          const float J = rn[tid] - cI, Q = rn[Win + tid] - cP;
+          kadd(sJ, J);
+          kadd(sQ, Q);
+          kadd(sJJ, J * J);
+          kadd(sJQ, J * Q);
+          if (y >= WIN) {
+            const float* ro = L.in + ((base + y - WIN) % Rin) * 2 * Win;
+            const float Jo = ro[tid] - cI, Qo = ro[Win + tid] - cP;
+            kadd(sJ, -Jo);
+            kadd(sQ, -Qo);
+            kadd(sJJ, -(Jo * Jo));
+            kadd(sJQ, -(Jo * Qo));
+          }
+          if (y >= 2 * RAD) {
+            float* v = L.vs + rho * 4 * Win;
+            v[tid] = kval(sJ);
+            v[Win + tid] = kval(sQ);
+            v[2 * Win + tid] = kval(sJJ);
+            v[3 * Win + tid] = kval(sJQ);
+          }
+        }
+      }
+      __syncthreads();
+      // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4) for stage-1 row y - r
+      {
+        const int runs = (w1_used + GF_C - 1) / GF_C;
+        for (int u = tid; u < rows * runs; u += blockDim.x) {
+          const int rho = u / runs, run = u - rho * runs;
+          const int y = r0 + rho;
+          if (y < 2 * RAD) continue;
+          const float* v = L.vs + rho * 4 * Win;
+          const int c0 = run * GF_C, c1 = min(c0 + GF_C, w1_used);
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+          for (int dd = 0; dd < WIN; ++dd) {
+            s0 += v[c0 + dd];
+            s1 += v[Win + c0 + dd];
+            s2 += v[2 * Win + c0 + dd];
+            s3 += v[3 * Win + c0 + dd];
+          }
+          float* abr = L.ab + ((base + y) % Rab) * 2 * W1;
+          for (int c = c0; c < c1; ++c) {
+            if (c > c0) {
+              s0 += v[c + 2 * RAD] - v[c - 1];
+              s1 += v[Win + c + 2 * RAD] - v[Win + c - 1];
+              s2 += v[2 * Win + c + 2 * RAD] - v[2 * Win + c - 1];
+              s3 += v[3 * Win + c + 2 * RAD] - v[3 * Win + c - 1];
+            }
+            const float mJ = s0 * inv_n, mQ = s1 * inv_n;
+            const float var = fmaf(-mJ, mJ, s2 * inv_n);  // sigma_k^2
+            const float cov = fmaf(-mJ, mQ, s3 * inv_n);  // mean(I p) - mu pbar
+            const float a = cov / (var + eps);
+            abr[c] = a;
+            abr[W1 + c] = (mQ + cP) - a * (mJ + cI);
+          }
+        }
+      }
+      __syncthreads();
+      // 3. column window sums of a and b (column tid of the a, b rows)
+      if (tid < w1_used) {
+        for (int rho = 0; rho < rows; ++rho) {
+          const int y = r0 + rho;
+          if (y < 2 * RAD) continue;
+          const float* an = L.ab + ((base + y) % Rab) * 2 * W1;
+          kadd(sa, an[tid]);
+          kadd(sb, an[W1 + tid]);
+          if (y >= 2 * RAD + WIN) {
+            const float* ao = L.ab + ((base + y - WIN) % Rab) * 2 * W1;
+            kadd(sa, -ao[tid]);
+            kadd(sb, -ao[W1 + tid]);
+          }
+          if (y >= 4 * RAD) {
+            float* v2 = L.vs2 + rho * 2 * W1;
+            v2[tid] = kval(sa);
+            v2[W1 + tid] = kval(sb);
+          }
+        }
+      }
+      __syncthreads();
+      // 4. row window sums -> u = abar I + bbar (Eq. 5) for output row y - 4r
+      {
+        const int runs = W / GF_C;
+        for (int u = tid; u < rows * runs; u += blockDim.x) {
+          const int rho = u / runs, run = u - rho * runs;
+          const int y = r0 + rho;
+          if (y < 4 * RAD) continue;
+          const float* v2 = L.vs2 + rho * 2 * W1;
+          const float* ri = L.in + ((base + y - 2 * RAD) % Rin) * 2 * Win;
+          const int x0r = run * GF_C;
+          float sa_ = 0.f, sb_ = 0.f;
+#pragma unroll
+          for (int dd = 0; dd < WIN; ++dd) {
+            sa_ += v2[x0r + dd];
+            sb_ += v2[W1 + x0r + dd];
+          }
+          const int gy = (y0 + y - 4 * RAD) & (M - 1);
+          float* urow = d.u + (size_t)gy * N;
+          const float* orow = uo ? uo + (size_t)gy * N : nullptr;
+#pragma unroll
+          for (int c = 0; c < GF_C; ++c) {
+            const int x = x0r + c;
+            if (c > 0) {
+              sa_ += v2[x + 2 * RAD] - v2[x - 1];
+              sb_ += v2[W1 + x + 2 * RAD] - v2[W1 + x - 1];
+            }
+            const float val = fmaf(sa_ * inv_n, ri[x + 2 * RAD], sb_ * inv_n);
+            const int gx = (x0 + x) & (N - 1);
+            urow[gx] = val;
+            if (orow) {
+              const float e = val - __ldg(&orow[gx]);
+              err = fmaf(e, e, err);
+            }
+          }
+        }
+      }
+    }
+    if (uo) {
+      // ||u - u_orig||^2 of this item (FP32 in a warp, FP64 across warps)
+      err = warp_sum(err);
+      if ((tid & 31) == 0) red[tid >> 5] = (double)err;
+      __syncthreads();
+      ImgState* S = st + gi;
+      if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < num_warps(); ++w) s += red[w];
+        atomicAdd(&S->err2, s);
+        __threadfence();
+        const unsigned int prev = atomicAdd(&S->gf_done, 1u);
+        *s_flag = (prev == (unsigned)per_img - 1);
+      }
+      __syncthreads();
+      if (*s_flag && tid == 0) {
+        __threadfence();
+        const double e2 = __ldcg(&S->err2);
+        d.isnr_out[iter] = 10.0 * log10(S->den_isnr / e2);
+        S->err2 = 0.0;
+        S->gf_done = 0;
+        __threadfence();
+      }
+    }
+    base = next_base;
+    item += gridDim.x;
   }
+  cp_async_wait<0>();
 }
 
 __global__ void __launch_bounds__(GF_THREADS)
 k_guided_filter(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
-                int plain_var) {
-  extern __shared__ float gsm[];
+                int plain_var, int rad, int W, int H) {
+  extern __shared__ __align__(16) float gsm[];
   __shared__ double red[GF_THREADS / 32];
   __shared__ int s_flag;
-  const int gi = cd.img0 + blockIdx.z;
-  const ImgDesc& d = imgs[gi];
-  const int M = cd.M, N = cd.N;
-  const int y0 = blockIdx.y * GF_T, x0 = blockIdx.x * GF_T;
-  const float* I = d.uI;
-  const float* p = d.up;
-  const float* uo = (iter >= 0 && d.isnr_out) ? d.uo : nullptr;
-  const float eps = (float)d.eps;
   const bool shifted = plain_var == 0;
-  float err = 0.0f;
-  switch ((d.w - 1) / 2) {
-    case 0: gf_tile<0>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 1: gf_tile<1>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 2: gf_tile<2>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 3: gf_tile<3>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 4: gf_tile<4>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 5: gf_tile<5>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 6: gf_tile<6>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    case 7: gf_tile<7>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-    default: gf_tile<8>(I, p, d.u, uo, M, N, y0, x0, eps, shifted, gsm, err); break;
-  }
-  if (uo == nullptr) return;
-  // ||u - u_orig||^2 for the ISNR of this iteration (FP32 in a warp, FP64 across)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) err += __shfl_xor_sync(0xffffffffu, err, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)err;
-  __syncthreads();
-  ImgState* S = st + gi;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < GF_THREADS / 32; ++w) s += red[w];
-    atomicAdd(&S->err2, s);
-    __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int nb = gridDim.x * gridDim.y;
-    const unsigned int prev = atomicAdd(&S->gf_done, 1u);
-    s_flag = (prev == nb - 1);
-  }
-  __syncthreads();
-  if (s_flag && threadIdx.x == 0) {
-    __threadfence();
-    const double e2 = __ldcg(&S->err2);
-    d.isnr_out[iter] = 10.0 * log10(S->den_isnr / e2);
-    S->err2 = 0.0;
-    S->gf_done = 0;
-    __threadfence();
+  switch (rad) {
+    case 0: gf_items<0>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 1: gf_items<1>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 2: gf_items<2>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 3: gf_items<3>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 4: gf_items<4>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 5: gf_items<5>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 6: gf_items<6>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    case 7: gf_items<7>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
+    default: gf_items<8>(cd, imgs, st, iter, shifted, W, H, gsm, red, &s_flag); break;
   }
 }
 
+static int gf_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+// One launch per window radius present in the class (the images of a class
+// are ordered by radius, so each group is a contiguous range).
 cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, cudaStream_t s) {
-  const int tx = (c.cd.N + GF_T - 1) / GF_T, ty = (c.cd.M + GF_T - 1) / GF_T;
-  const size_t smem = gf_smem_floats(c.max_rad) * sizeof(float);
-  k_guided_filter<<<dim3(tx, ty, c.cd.n_img), GF_THREADS, smem, s>>>(c.cd, c.imgs, c.st, iter,
-                                                                      plain_var);
+  const int W = c.cd.N < GF_W ? c.cd.N : GF_W;
+  const int H = c.cd.M < GF_H ? c.cd.M : GF_H;
+  for (int g = 0; g < c.n_rad_groups; ++g) {
+    const RadGroup& rg = c.rad_groups[g];
+    ClassDesc cd = c.cd;
+    cd.img0 = rg.img0;
+    cd.n_img = rg.n_img;
+    const size_t smem = gf_smem_floats(rg.rad) * sizeof(float);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_guided_filter, GF_THREADS, smem) !=
+            cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    const int n_items = cd.n_img * (cd.N / W) * (cd.M / H);
+    int grid = per_sm * gf_sm_count();
+    if (grid > n_items) grid = n_items;
+    k_guided_filter<<<grid, GF_THREADS, smem, s>>>(cd, c.imgs, c.st, iter, plain_var, rg.rad, W, H);
+  }
   return cudaGetLastError();
 }
 

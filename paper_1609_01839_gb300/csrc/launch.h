@@ -32,12 +32,19 @@ struct Tables {
   const float* d2;    // 4 sin^2(pi m / 4096)
 };
 
+// Images of a class sharing one guided-filter radius (contiguous range).
+struct RadGroup {
+  int img0, n_img, rad;
+};
+
 // Everything a launch needs about one size class.
 struct ClassLaunch {
   ClassDesc cd;
   const ImgDesc* imgs;  // device array (whole batch)
   ImgState* st;         // device array (whole batch)
   int max_rad;          // largest guided-filter radius in the class
+  int n_rad_groups;
+  RadGroup rad_groups[9];
 };
 
 // Row pass of the 2-D real DFT: real plane src -> packed rows dst.
