@@ -24,16 +24,18 @@ namespace gfd {
 constexpr int GF_W = 128;      // output columns per item (at most N)
 constexpr int GF_H = 128;      // output rows per item (at most M)
 constexpr int GF_RB = 8;       // input rows per batch
-constexpr int GF_C = 4;        // columns per thread in the row sums
+constexpr int GF_C = 8;        // columns per thread in the row sums
 constexpr int GF_THREADS = 256;
 constexpr int GF_RMAX = 8;     // w <= 17
 
+// Row pitches are 1 (mod 32) so that rows fall on consecutive banks.
+GFD_HD int gf_pitch(int w) { return ((w + 30) / 32) * 32 + 1; }
 GFD_HD int gf_rin(int rad) { return 2 * GF_RB + 2 * rad + 1; }
 GFD_HD int gf_rab(int rad) { return GF_RB + 2 * rad + 1; }
 GFD_HD size_t gf_smem_floats(int rad) {
-  const int Win = GF_W + 4 * rad, W1 = GF_W + 2 * rad;
-  return (size_t)gf_rin(rad) * 2 * Win + (size_t)GF_RB * 4 * Win + (size_t)gf_rab(rad) * 2 * W1 +
-         (size_t)GF_RB * 2 * W1;
+  const int Wp = gf_pitch(GF_W + 4 * rad), W1p = gf_pitch(GF_W + 2 * rad);
+  return (size_t)2 * gf_rin(rad) * Wp + (size_t)4 * GF_RB * Wp + (size_t)2 * gf_rab(rad) * W1p +
+         (size_t)2 * GF_RB * W1p;
 }
 
 struct Kahan {
@@ -52,22 +54,26 @@ GFD_D void cp_async4(void* smem_dst, const void* gsrc) {
                : "memory");
 }
 
+// Shared-memory arrays, plane-major, rows of pitch Wp (input columns) or
+// W1p (columns of a, b).  The row-sum stages give lane l the batch row
+// l % GF_RB and a run of GF_C columns, so a warp touches 8 rows x 4 runs at
+// distinct banks.
 template <int RAD>
 struct GfLayout {
   static constexpr int WIN = 2 * RAD + 1;
-  static constexpr int Win = GF_W + 4 * RAD;  // input columns
-  static constexpr int W1 = GF_W + 2 * RAD;   // columns of a, b
+  static constexpr int Wp = ((GF_W + 4 * RAD + 30) / 32) * 32 + 1;
+  static constexpr int W1p = ((GF_W + 2 * RAD + 30) / 32) * 32 + 1;
   static constexpr int Rin = 2 * GF_RB + 2 * RAD + 1;
   static constexpr int Rab = GF_RB + 2 * RAD + 1;
-  float* in;   // [Rin][2][Win]   input rows (I, p)
-  float* vs;   // [RB][4][Win]    column window sums of the batch rows
-  float* ab;   // [Rab][2][W1]    a, b rows
-  float* vs2;  // [RB][2][W1]     column window sums of a, b
+  float* in;   // [2][Rin][Wp]   input rows (I, p), ring
+  float* vs;   // [4][RB][Wp]    column window sums of the batch rows
+  float* ab;   // [2][Rab][W1p]  a, b rows, ring
+  float* vs2;  // [2][RB][W1p]   column window sums of a, b
   GFD_D explicit GfLayout(float* sm) {
     in = sm;
-    vs = in + Rin * 2 * Win;
-    ab = vs + GF_RB * 4 * Win;
-    vs2 = ab + Rab * 2 * W1;
+    vs = in + 2 * Rin * Wp;
+    ab = vs + 4 * GF_RB * Wp;
+    vs2 = ab + 2 * Rab * W1p;
   }
 };
 
@@ -75,7 +81,7 @@ template <int RAD>
 GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
                     bool shifted, int W, int H, float* sm, double* red, int* s_flag) {
   using Lay = GfLayout<RAD>;
-  constexpr int WIN = Lay::WIN, Win = Lay::Win, W1 = Lay::W1, Rin = Lay::Rin, Rab = Lay::Rab;
+  constexpr int WIN = Lay::WIN, Wp = Lay::Wp, W1p = Lay::W1p, Rin = Lay::Rin, Rab = Lay::Rab;
   const Lay L(sm);
   const int M = cd.M, N = cd.N;
   const int tid = threadIdx.x;
@@ -104,7 +110,7 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
         const int gy = (y0 - 2 * RAD + r0 + row) & (M - 1);
         const int gx = (x0 - 2 * RAD + c) & (N - 1);
         const float* src = (plane == 0 ? d.uI : d.up) + (size_t)gy * N + gx;
-        cp_async4(L.in + ((base + r0 + row) % Rin) * 2 * Win + plane * Win + c, src);
+        cp_async4(L.in + (plane * Rin + (base + r0 + row) % Rin) * Wp + c, src);
       }
     }
     cp_async_commit();
@@ -142,26 +148,27 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
       if (tid < win_used) {
         for (int rho = 0; rho < rows; ++rho) {
           const int y = r0 + rho;
-          const float* rn = L.in + ((base + y) % Rin) * 2 * Win;
-          const float J = rn[tid] - cI, Q = rn[Win + tid] - cP;
+          const float* rn = L.in + ((base + y) % Rin) * Wp;
+          const float J = rn[tid] - cI, Q = rn[Rin * Wp + tid] - cP;
           kadd(sJ, J);
           kadd(sQ, Q);
           kadd(sJJ, J * J);
           kadd(sJQ, J * Q);
           if (y >= WIN) {
-            const float* ro = L.in + ((base + y - WIN) % Rin) * 2 * Win;
-            const float Jo = ro[tid] - cI, Qo = ro[Win + tid] - cP;
+            const float* ro = L.in + ((base + y - WIN) % Rin) * Wp;
+            const float Jo = ro[tid] - cI, Qo = ro[Rin * Wp + tid] - cP;
             kadd(sJ, -Jo);
             kadd(sQ, -Qo);
             kadd(sJJ, -(Jo * Jo));
             kadd(sJQ, -(Jo * Qo));
           }
           if (y >= 2 * RAD) {
-            float* v = L.vs + rho * 4 * Win;
+            float* v = L.vs + rho * Wp;
+            constexpr int PS = GF_RB * Wp;  // plane stride
             v[tid] = kval(sJ);
-            v[Win + tid] = kval(sQ);
-            v[2 * Win + tid] = kval(sJJ);
-            v[3 * Win + tid] = kval(sJQ);
+            v[PS + tid] = kval(sQ);
+            v[2 * PS + tid] = kval(sJJ);
+            v[3 * PS + tid] = kval(sJQ);
           }
         }
       }
@@ -169,34 +176,35 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
       // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4) for stage-1 row y - r
       {
         const int runs = (w1_used + GF_C - 1) / GF_C;
-        for (int u = tid; u < rows * runs; u += blockDim.x) {
-          const int rho = u / runs, run = u - rho * runs;
+        constexpr int PS = GF_RB * Wp;
+        for (int u = tid; u < GF_RB * runs; u += blockDim.x) {
+          const int rho = u % GF_RB, run = u / GF_RB;
           const int y = r0 + rho;
-          if (y < 2 * RAD) continue;
-          const float* v = L.vs + rho * 4 * Win;
+          if (rho >= rows || y < 2 * RAD) continue;
+          const float* v = L.vs + rho * Wp;
           const int c0 = run * GF_C, c1 = min(c0 + GF_C, w1_used);
           float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
           for (int dd = 0; dd < WIN; ++dd) {
             s0 += v[c0 + dd];
-            s1 += v[Win + c0 + dd];
-            s2 += v[2 * Win + c0 + dd];
-            s3 += v[3 * Win + c0 + dd];
+            s1 += v[PS + c0 + dd];
+            s2 += v[2 * PS + c0 + dd];
+            s3 += v[3 * PS + c0 + dd];
           }
-          float* abr = L.ab + ((base + y) % Rab) * 2 * W1;
+          float* abr = L.ab + ((base + y) % Rab) * W1p;
           for (int c = c0; c < c1; ++c) {
             if (c > c0) {
               s0 += v[c + 2 * RAD] - v[c - 1];
-              s1 += v[Win + c + 2 * RAD] - v[Win + c - 1];
-              s2 += v[2 * Win + c + 2 * RAD] - v[2 * Win + c - 1];
-              s3 += v[3 * Win + c + 2 * RAD] - v[3 * Win + c - 1];
+              s1 += v[PS + c + 2 * RAD] - v[PS + c - 1];
+              s2 += v[2 * PS + c + 2 * RAD] - v[2 * PS + c - 1];
+              s3 += v[3 * PS + c + 2 * RAD] - v[3 * PS + c - 1];
             }
             const float mJ = s0 * inv_n, mQ = s1 * inv_n;
             const float var = fmaf(-mJ, mJ, s2 * inv_n);  // sigma_k^2
             const float cov = fmaf(-mJ, mQ, s3 * inv_n);  // mean(I p) - mu pbar
             const float a = cov / (var + eps);
             abr[c] = a;
-            abr[W1 + c] = (mQ + cP) - a * (mJ + cI);
+            abr[Rab * W1p + c] = (mQ + cP) - a * (mJ + cI);
           }
         }
       }
@@ -206,18 +214,18 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
         for (int rho = 0; rho < rows; ++rho) {
           const int y = r0 + rho;
           if (y < 2 * RAD) continue;
-          const float* an = L.ab + ((base + y) % Rab) * 2 * W1;
+          const float* an = L.ab + ((base + y) % Rab) * W1p;
           kadd(sa, an[tid]);
-          kadd(sb, an[W1 + tid]);
+          kadd(sb, an[Rab * W1p + tid]);
           if (y >= 2 * RAD + WIN) {
-            const float* ao = L.ab + ((base + y - WIN) % Rab) * 2 * W1;
+            const float* ao = L.ab + ((base + y - WIN) % Rab) * W1p;
             kadd(sa, -ao[tid]);
-            kadd(sb, -ao[W1 + tid]);
+            kadd(sb, -ao[Rab * W1p + tid]);
           }
           if (y >= 4 * RAD) {
-            float* v2 = L.vs2 + rho * 2 * W1;
+            float* v2 = L.vs2 + rho * W1p;
             v2[tid] = kval(sa);
-            v2[W1 + tid] = kval(sb);
+            v2[GF_RB * W1p + tid] = kval(sb);
           }
         }
       }
@@ -225,18 +233,19 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
       // 4. row window sums -> u = abar I + bbar (Eq. 5) for output row y - 4r
       {
         const int runs = W / GF_C;
-        for (int u = tid; u < rows * runs; u += blockDim.x) {
-          const int rho = u / runs, run = u - rho * runs;
+        constexpr int PS2 = GF_RB * W1p;
+        for (int u = tid; u < GF_RB * runs; u += blockDim.x) {
+          const int rho = u % GF_RB, run = u / GF_RB;
           const int y = r0 + rho;
-          if (y < 4 * RAD) continue;
-          const float* v2 = L.vs2 + rho * 2 * W1;
-          const float* ri = L.in + ((base + y - 2 * RAD) % Rin) * 2 * Win;
+          if (rho >= rows || y < 4 * RAD) continue;
+          const float* v2 = L.vs2 + rho * W1p;
+          const float* ri = L.in + ((base + y - 2 * RAD) % Rin) * Wp;
           const int x0r = run * GF_C;
           float sa_ = 0.f, sb_ = 0.f;
 #pragma unroll
           for (int dd = 0; dd < WIN; ++dd) {
             sa_ += v2[x0r + dd];
-            sb_ += v2[W1 + x0r + dd];
+            sb_ += v2[PS2 + x0r + dd];
           }
           const int gy = (y0 + y - 4 * RAD) & (M - 1);
           float* urow = d.u + (size_t)gy * N;
@@ -246,7 +255,7 @@ GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgSt
             const int x = x0r + c;
             if (c > 0) {
               sa_ += v2[x + 2 * RAD] - v2[x - 1];
-              sb_ += v2[W1 + x + 2 * RAD] - v2[W1 + x - 1];
+              sb_ += v2[PS2 + x + 2 * RAD] - v2[PS2 + x - 1];
             }
             const float val = fmaf(sa_ * inv_n, ri[x + 2 * RAD], sb_ * inv_n);
             const int gx = (x0 + x) & (N - 1);
