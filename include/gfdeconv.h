@@ -15,6 +15,9 @@
  *   - Buffers named "device" are CUDA device pointers on the context's device,
  *     owned by the caller; the library never frees or retains them after the
  *     call's stream work completes.  The library owns only its workspace.
+ *     Device image buffers (observations, outputs, u_orig, u_init, spectra)
+ *     must start on a 16-byte boundary (cudaMalloc and PyTorch allocations
+ *     do); a misaligned one is rejected with GFD_ERR_INVALID_ARG.
  *   - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t;
  *     NULL = the legacy default stream) unless stated otherwise.  Argument
  *     errors are returned synchronously, before any launch.  Conditions found

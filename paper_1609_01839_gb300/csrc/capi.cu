@@ -100,6 +100,16 @@ int map_err(cudaError_t e) {
   return GFD_ERR_CUDA;
 }
 
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Device image planes are read and written with 16-byte accesses.
+int validate_device_planes(const gfdeconv_image& im) {
+  if (!aligned16(im.y) || !aligned16(im.u_out) || !aligned16(im.u_orig) || !aligned16(im.u_init) ||
+      !aligned16(im.uI_out) || !aligned16(im.up_out))
+    return GFD_ERR_INVALID_ARG;
+  return GFD_OK;
+}
+
 int validate_image(const gfdeconv_image& im, int iters) {
   if (!im.y || !im.h || !im.u_out) return GFD_ERR_INVALID_ARG;
   if (!pow2_in(im.M, 8, 4096) || !pow2_in(im.N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
@@ -515,7 +525,8 @@ int gfdeconv_solve_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, i
                            void* stream) {
   if (!c || !imgs || n <= 0) return GFD_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
-    const int r = validate_image(imgs[i], iters);
+    int r = validate_image(imgs[i], iters);
+    if (r == GFD_OK) r = validate_device_planes(imgs[i]);
     if (r != GFD_OK) return r;
   }
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
@@ -526,7 +537,8 @@ int gfdeconv_solve_batched_timed(gfdeconv_ctx* c, int n, const gfdeconv_image* i
                                  void* stream, double* phase_ms, long long* phase_launches) {
   if (!c || !imgs || n <= 0 || !phase_ms || !phase_launches) return GFD_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
-    const int r = validate_image(imgs[i], iters);
+    int r = validate_image(imgs[i], iters);
+    if (r == GFD_OK) r = validate_device_planes(imgs[i]);
     if (r != GFD_OK) return r;
   }
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
@@ -678,6 +690,7 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
 int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, int N, int w,
                         double eps, float* u_out, void* stream) {
   if (!c || !I || !p || !u_out) return GFD_ERR_INVALID_ARG;
+  if (!aligned16(I) || !aligned16(p) || !aligned16(u_out)) return GFD_ERR_INVALID_ARG;
   if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
   if (!std::isfinite(eps)) return GFD_ERR_NONFINITE_INPUT;
   if (!(eps > 0.0) || w < 1 || w > 17 || !(w & 1)) return GFD_ERR_INVALID_ARG;
@@ -707,6 +720,7 @@ int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, 
 
 int gfdeconv_fft2_r2c(gfdeconv_ctx* c, const float* x, int M, int N, float* X, void* stream) {
   if (!c || !x || !X) return GFD_ERR_INVALID_ARG;
+  if (!aligned16(x) || !aligned16(X)) return GFD_ERR_INVALID_ARG;
   if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -731,6 +745,7 @@ int gfdeconv_fft2_r2c(gfdeconv_ctx* c, const float* x, int M, int N, float* X, v
 
 int gfdeconv_fft2_c2r(gfdeconv_ctx* c, const float* X, int M, int N, float* x, void* stream) {
   if (!c || !x || !X) return GFD_ERR_INVALID_ARG;
+  if (!aligned16(x) || !aligned16(X)) return GFD_ERR_INVALID_ARG;
   if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
