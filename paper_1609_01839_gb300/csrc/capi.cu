@@ -306,7 +306,7 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   }
   for (auto& cl : pl.classes) {
     GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));
-    ++L;
+    L += 2;  // k_setup_init, k_zero_parts
   }
   for (auto& cl : pl.classes) {
     GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
@@ -341,7 +341,7 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
       GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
                                               1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
       GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
-      L += 3;
+      L += 2 + cl.n_rad_groups;  // one guided-filter launch per window radius
     }
   }
   for (int i = 0; i < pl.n; ++i) {

@@ -1,7 +1,7 @@
 """GPU parity: every step of the CUDA path, called through the C-ABI, against
 the FP64 oracle on the same seeded inputs.
 
-Tolerances (written here, derived in the design doc):
+Tolerances:
   u          max-abs 2e-5 on [0, 1] images, per iteration
   lambda     1e-6 relative on a teacher-forced step (the GPU step fed the
              oracle's own u_E^k); along a free trajectory the GPU's u_E drifts
@@ -13,7 +13,7 @@ Tolerances (written here, derived in the design doc):
              (about sigma^2 per pixel) formed from FP32 spectra whose absolute
              error is about eps32 * sqrt(log2 P) * ||u_E||, so a few 1e-6 of
              it is the FP32 floor
-Measured errors are appended to gpurun_out/parity_metrics.jsonl.
+Measured errors are appended to parity_metrics.jsonl in the run's output folder.
 """
 import math
 
