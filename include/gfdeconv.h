@@ -45,7 +45,8 @@ typedef enum {
   GFD_ERR_ALLOC = -4,            /* workspace allocation failed */
   GFD_ERR_CUDA = -5,             /* a CUDA runtime call failed */
   GFD_ERR_NONCONVERGED = -6,     /* (status) lambda root outside the bracket */
-  GFD_ERR_TIMEOUT = -7           /* reserved: no entry point waits on the device */
+  GFD_ERR_TIMEOUT = -7,          /* reserved: no entry point waits on the device */
+  GFD_ERR_SCRATCH_LIMIT = -8     /* gfdeconv_fft2_r2c_noalloc: M*N above its static scratch */
 } gfd_status;
 
 /* Per-image status bits returned by gfdeconv_status(). */
@@ -127,6 +128,35 @@ int gfdeconv_guidfilter(gfdeconv_ctx* ctx, const float* I, const float* p, int M
  * X[m][0] = F(x)(m, 0) + i F(x)(m, N/2).  The DFT diagonalises the circular
  * operators of Sec. 3.1. */
 int gfdeconv_fft2_r2c(gfdeconv_ctx* ctx, const float* x, int M, int N, float* X, void* stream);
+
+/* gfdeconv_fft2_r2c without any allocation.  The paper has no counterpart:
+ * this is an interface variant, not a step of the method.
+ *
+ * Same arguments, result and layout as gfdeconv_fft2_r2c, but the call makes
+ * no cudaMalloc / cudaFree and calls no allocating library: its intermediate
+ * row-pass plane and its kernel descriptor live in one file-scope
+ * `static __device__ __align__(256)` array of GFD_NOALLOC_SCRATCH_BYTES,
+ * allocated when the library's device code is loaded.  It serves callers that
+ * must not allocate on the device: code running under a memory budget that a
+ * caching allocator has already claimed in full (a cudaMalloc can fail there
+ * although the caller has room in its own pool), and latency-bound loops for
+ * which the workspace growth of gfdeconv_fft2_r2c (cudaFree synchronises the
+ * whole device) is not acceptable.
+ *
+ * Limit: M*N <= GFD_NOALLOC_MAX_PIXELS (1024 x 1024); larger sizes return
+ * GFD_ERR_SCRATCH_LIMIT before any work.  The first call on each device looks
+ * up the scratch address with cudaGetSymbolAddress and caches it: make that
+ * first call outside any stream capture.  Nothing in the scratch has to start
+ * at zero: every call writes the descriptor and the whole intermediate plane
+ * before reading them.  The scratch is shared by every call on a device, so
+ * calls whose stream work overlaps (different streams, or different host
+ * threads without ordering between them) race on it: order them on one stream
+ * or synchronise between them.  ctx must be a live context (its twiddle table
+ * is used; the context allocates nothing here either). */
+#define GFD_NOALLOC_MAX_PIXELS (1024 * 1024)
+#define GFD_NOALLOC_SCRATCH_BYTES (256 + 4 * GFD_NOALLOC_MAX_PIXELS)
+int gfdeconv_fft2_r2c_noalloc(gfdeconv_ctx* ctx, const float* x, int M, int N, float* X,
+                              void* stream);
 
 /* Inverse of gfdeconv_fft2_r2c: x = (1/(M N)) * inverse DFT of the packed
  * half spectrum X (a Hermitian spectrum is assumed). */

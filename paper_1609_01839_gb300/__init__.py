@@ -27,6 +27,7 @@ STATUS_NONCONVERGED = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_PSF = 4
 STATUS_BAD_RHO = 8
+ERR_SCRATCH_LIMIT = -8  # gfdeconv_fft2_r2c_noalloc: M*N above its static scratch
 NUM_PHASES = 8
 PHASES = ("setup", "row_fwd", "col_fwd_lambda", "lambda_pass", "col_solve_inv", "row_inv",
           "guided_filter", "copy")
@@ -83,6 +84,7 @@ def _load():
         "gfdeconv_guidfilter": (ci, [vp, vp, vp, ci, ci, ci, cd, vp, vp]),
         "gfdeconv_fft2_r2c": (ci, [vp, vp, ci, ci, vp, vp]),
         "gfdeconv_fft2_c2r": (ci, [vp, vp, ci, ci, vp, vp]),
+        "gfdeconv_fft2_r2c_noalloc": (ci, [vp, vp, ci, ci, vp, vp]),
         "gfdeconv_solve_batched_timed": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp,
                                               ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_longlong)]),
         "gfdeconv_status": (ci, [vp, ctypes.POINTER(ci), ci]),
@@ -301,6 +303,18 @@ class Context:
                                     _stream(stream))
         if rc != 0:
             raise GfdError(rc, "gfdeconv_fft2_r2c")
+        return X
+
+    def fft2_r2c_noalloc(self, x, X, stream=None):
+        """gfdeconv_fft2_r2c_noalloc into the caller's complex64 (M, N/2)
+        tensor X (the library allocates nothing; M*N <= 1024*1024)."""
+        import torch
+        M, N = x.shape
+        rc = _lib.gfdeconv_fft2_r2c_noalloc(self._h, _ptr(x, "x", torch.float32), M, N,
+                                            _ptr(X, "X", torch.complex64, M * (N // 2)),
+                                            _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_fft2_r2c_noalloc")
         return X
 
     def fft2_c2r(self, X, stream=None):

@@ -448,6 +448,8 @@ const char* gfdeconv_strerror(int code) {
     case GFD_ERR_CUDA: return "CUDA runtime error";
     case GFD_ERR_NONCONVERGED: return "regularisation parameter did not converge";
     case GFD_ERR_TIMEOUT: return "timeout";
+    case GFD_ERR_SCRATCH_LIMIT:
+      return "size exceeds the static scratch of gfdeconv_fft2_r2c_noalloc (M*N <= 1024*1024)";
     default: return "unknown error";
   }
 }
@@ -794,3 +796,56 @@ const char* gfdeconv_last_cuda_error(void) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free 2-D real DFT (no counterpart in the paper).  The descriptor
+// and the packed row-pass plane live in a static device array; the descriptor
+// is written by a one-thread kernel from its by-value argument, so no host
+// buffer is involved either.
+namespace gfd {
+namespace {
+
+static_assert(sizeof(ImgDesc) <= 256, "descriptor slot");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GFD_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+__global__ void k_store_desc(ImgDesc d, ImgDesc* dst) { *dst = d; }
+
+}  // namespace
+}  // namespace gfd
+
+int gfdeconv_fft2_r2c_noalloc(gfdeconv_ctx* c, const float* x, int M, int N, float* X,
+                              void* stream) {
+  using namespace gfd;
+  if (!c || !x || !X) return GFD_ERR_INVALID_ARG;
+  if (!aligned16(x) || !aligned16(X)) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if ((long long)M * N > GFD_NOALLOC_MAX_PIXELS) return GFD_ERR_SCRATCH_LIMIT;
+  if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaError_t e;
+  if (!g_noalloc_addr[c->device]) {
+    void* p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return map_err(e);
+    g_noalloc_addr[c->device] = p;
+  }
+  char* base = static_cast<char*>(g_noalloc_addr[c->device]);
+  cudaStream_t s = (cudaStream_t)stream;
+  ImgDesc d{};
+  d.u = const_cast<float*>(x);
+  d.S = reinterpret_cast<float2*>(base + 256);
+  d.Y = reinterpret_cast<float2*>(X);
+  ImgDesc* d_desc = reinterpret_cast<ImgDesc*>(base);
+  k_store_desc<<<1, 1, 0, s>>>(d, d_desc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return map_err(e);
+  ClassLaunch cl{};
+  cl.cd = ClassDesc{M, N, 1, 0, N / 2};
+  cl.imgs = d_desc;
+  cl.st = nullptr;  // the plain passes keep no per-image state
+  const Tables t{c->tw, c->d2};
+  if ((e = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s)) != cudaSuccess) return map_err(e);
+  if ((e = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s)) != cudaSuccess) return map_err(e);
+  return GFD_OK;
+}
