@@ -478,20 +478,23 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
     delete c;
     return map_err(e);
   }
-  // twiddles W_4096^m and gradient weights 4 sin^2(pi m / 4096), in double, rounded once
-  std::vector<float2> tw(TW_N);
-  std::vector<float> d2(TW_N);
+  // twiddles W_L^m and gradient weights 4 sin^2(pi m / L) for every
+  // power-of-two L <= 4096 (size L at offset L - 2), in double, rounded once
+  std::vector<float2> tw(TAB_ENTRIES);
+  std::vector<float> d2(TAB_ENTRIES);
   const double pi = 3.14159265358979323846;
-  for (int m = 0; m < TW_N; ++m) {
-    const double th = 2.0 * pi * m / TW_N;
-    tw[m] = make_float2((float)std::cos(th), (float)-std::sin(th));
-    const double sn = std::sin(pi * m / TW_N);
-    d2[m] = (float)(4.0 * sn * sn);
+  for (int L = 2; L <= TW_N; L *= 2) {
+    for (int m = 0; m < L; ++m) {
+      const double th = 2.0 * pi * m / L;
+      tw[tab_off(L) + m] = make_float2((float)std::cos(th), (float)-std::sin(th));
+      const double sn = std::sin(pi * m / L);
+      d2[tab_off(L) + m] = (float)(4.0 * sn * sn);
+    }
   }
-  if ((e = cudaMalloc(&c->tw, sizeof(float2) * TW_N)) != cudaSuccess ||
-      (e = cudaMalloc(&c->d2, sizeof(float) * TW_N)) != cudaSuccess ||
-      (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * TW_N, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(c->d2, d2.data(), sizeof(float) * TW_N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e = cudaMalloc(&c->tw, sizeof(float2) * TAB_ENTRIES)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d2, sizeof(float) * TAB_ENTRIES)) != cudaSuccess ||
+      (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(c->d2, d2.data(), sizeof(float) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMalloc(&c->aux_st, sizeof(ImgState))) != cudaSuccess ||
       (e = cudaMemset(c->aux_st, 0, sizeof(ImgState))) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) {

@@ -15,6 +15,11 @@ namespace gfd {
 // tw[x * (4096 / L)].
 constexpr int TW_LOG2 = 12;
 constexpr int TW_N = 1 << TW_LOG2;
+// Per-size tables: for every L = 2, 4, ..., TW_N the L entries of size L
+// (W_L^m = exp(-2 pi i m / L), or 4 sin^2(pi m / L)) start at offset L - 2, so
+// a transform of length L touches one compact table of L entries.
+constexpr int TAB_ENTRIES = 2 * TW_N - 2;
+GFD_HD int tab_off(int L) { return L - 2; }
 
 // Number of interpolation nodes for the regularisation-parameter equation
 // (Sec. 3.2, Eq. 11) evaluated per spectral pass.

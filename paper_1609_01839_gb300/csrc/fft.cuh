@@ -49,6 +49,11 @@ constexpr int num_stages(int L, int R) {
 GFD_HD int phys(int a) { return a + (a >> 4); }
 // elements of one team's buffer (odd, so that teams interleave across banks)
 GFD_HD int team_stride(int L) { return L + (L >> 4) + 1; }
+// Buffer stride of the B interleaved column teams of a column pass.  Loads
+// and stores that walk B columns fastest put B columns x 16/B consecutive
+// elements in a half-warp; a stride of 16/B (mod 16) float2 places them on
+// distinct bank pairs.
+GFD_HD int col_team_stride(int L, int B) { return L + (L >> 4) + (B < 16 ? 16 / B : 1); }
 
 // cos / sin of 2 pi m / 16
 __device__ constexpr float kCos16[16] = {
@@ -114,8 +119,9 @@ struct DFT<2, INV> {
   }
 };
 
-GFD_D float2 twiddle(const float2* __restrict__ tw, int idx4096, bool inv) {
-  float2 w = __ldg(&tw[idx4096]);
+// tw: the table of the transform length L (W_L^m, m < L)
+GFD_D float2 twiddle(const float2* __restrict__ tw, int m, bool inv) {
+  float2 w = __ldg(&tw[m]);
   if (inv) w.y = -w.y;
   return w;
 }
@@ -141,7 +147,7 @@ struct Stage {
       constexpr int r = Ls < R ? Ls : R;
       constexpr int Ln = Ls / r;
       constexpr int T = L / R;
-      constexpr int twstep = TW_N / Ls;
+      constexpr int twstep = L / Ls;  // W_Ls = W_L^(L / Ls)
 #pragma unroll
       for (int q = 0; q < R / r; ++q) {
         const int beta = j + T * q;
@@ -165,6 +171,50 @@ struct Stage {
   }
 };
 
+// Two transforms of the same length on one team (buffers A and B), stage by
+// stage: each butterfly's twiddles are loaded once and applied to both.
+template <int L, int R, bool INV, int s>
+struct Stage2 {
+  template <class Idx>
+  GFD_D static void run(float2* bufA, float2* bufB, int j, const float2* __restrict__ tw, Idx idx) {
+    constexpr int Ls = stage_len(L, R, s);
+    if constexpr (Ls > 1) {
+      constexpr int r = Ls < R ? Ls : R;
+      constexpr int Ln = Ls / r;
+      constexpr int T = L / R;
+      constexpr int twstep = L / Ls;
+#pragma unroll
+      for (int q = 0; q < R / r; ++q) {
+        const int beta = j + T * q;
+        const int g = beta / Ln;
+        const int jj = beta % Ln;
+        const int base = g * Ls + jj;
+        float2 w[r];
+        if constexpr (Ln > 1) {
+#pragma unroll
+          for (int i = 1; i < r; ++i) w[i] = twiddle(tw, jj * i * twstep, INV);
+        }
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float2* buf = h ? bufB : bufA;
+          float2 x[r];
+#pragma unroll
+          for (int i = 0; i < r; ++i) x[i] = buf[idx(base + i * Ln)];
+          DFT<r, INV>::run(x);
+          if constexpr (Ln > 1) {
+#pragma unroll
+            for (int i = 1; i < r; ++i) x[i] = cmul(x[i], w[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < r; ++i) buf[idx(base + i * Ln)] = x[i];
+        }
+      }
+      __syncthreads();
+      Stage2<L, R, INV, s + 1>::run(bufA, bufB, j, tw, idx);
+    }
+  }
+};
+
 // First stage reading from a separate (landing) buffer `in` addressed by
 // iidx, writing to buf addressed by idx; the remaining stages run in buf.
 template <int L, int R, bool INV>
@@ -176,7 +226,7 @@ struct Stage0From {
     constexpr int r = Ls < R ? Ls : R;
     constexpr int Ln = Ls / r;
     constexpr int T = L / R;
-    constexpr int twstep = TW_N / Ls;
+    constexpr int twstep = L / Ls;
 #pragma unroll
     for (int q = 0; q < R / r; ++q) {
       const int beta = j + T * q;
@@ -217,6 +267,13 @@ GFD_D void fft_team(float2* buf, int j, const float2* __restrict__ tw, Idx idx =
   Stage<L, radix_for(L), INV, 0>::run(buf, j, tw, idx);
 }
 
+// fft_team on two buffers of the same team at once (shared twiddles).
+template <int L, bool INV, class Idx = PaddedIdx>
+GFD_D void fft_team2(float2* bufA, float2* bufB, int j, const float2* __restrict__ tw,
+                     Idx idx = Idx()) {
+  Stage2<L, radix_for(L), INV, 0>::run(bufA, bufB, j, tw, idx);
+}
+
 // position of output k after the in-place stages (digit reversal)
 template <int L>
 GFD_D int out_pos(int k) {
@@ -231,6 +288,23 @@ GFD_D int out_pos(int k) {
     rem /= r;
   }
   return p;
+}
+
+// inverse of out_pos: the output index stored at position p
+template <int L>
+GFD_D int in_pos(int p) {
+  constexpr int R = radix_for(L);
+  constexpr int S = num_stages(L, R);
+  int k = 0, mul = 1, rem = p;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int r = stage_radix(L, R, s);
+    const int Ln = stage_len(L, R, s) / r;
+    k += (rem / Ln) * mul;
+    rem %= Ln;
+    mul *= r;
+  }
+  return k;
 }
 
 }  // namespace gfd

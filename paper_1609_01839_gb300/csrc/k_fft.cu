@@ -93,7 +93,7 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
       part = warp_sum(part);
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)part;
     }
-    fft_team_from<L, false>(in, IdentIdx(), buf, j, tw);  // first stage reads land
+    fft_team_from<L, false>(in, IdentIdx(), buf, j, tw + tab_off(L));  // first stage reads land
     issue(item + gridDim.x);                               // land is free again
     if (do_sum && threadIdx.x == 0) {
       double s = 0.0;
@@ -113,7 +113,7 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
         const float2 E = cscale(cadd(Zk, Zm), 0.5f);
         const float2 D = csub(Zk, Zm);
         const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
-        out = cadd(E, cmul(__ldg(&tw[k * (TW_N / N)]), O));
+        out = cadd(E, cmul(__ldg(&tw[tab_off(N) + k]), O));
       }
       ob[k] = out;
     }
@@ -194,19 +194,19 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
         const float2 Rk = in[k], Rm = in[km];
         {
           const float2 E = cadd(Rk, cconj(Rm));
-          const float2 O = cmul(csub(Rk, cconj(Rm)), cconj(__ldg(&tw[k * (TW_N / N)])));
+          const float2 O = cmul(csub(Rk, cconj(Rm)), cconj(__ldg(&tw[tab_off(N) + k])));
           buf[phys(k)] = make_float2(E.x - O.y, E.y + O.x);
         }
         if (km != k) {
           const float2 E = cadd(Rm, cconj(Rk));
-          const float2 O = cmul(csub(Rm, cconj(Rk)), cconj(__ldg(&tw[km * (TW_N / N)])));
+          const float2 O = cmul(csub(Rm, cconj(Rk)), cconj(__ldg(&tw[tab_off(N) + km])));
           buf[phys(km)] = make_float2(E.x - O.y, E.y + O.x);
         }
       }
     }
     __syncthreads();
     issue(item + gridDim.x);
-    fft_team<L, true>(buf, j, tw);
+    fft_team<L, true>(buf, j, tw + tab_off(L));
     float2* rowp = reinterpret_cast<float2*>(real_plane(d, dsel)) + (size_t)row * L;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -234,7 +234,11 @@ GFD_D void issue_tile(float2* dst, const float2* src, int M, int TB, int B) {
 }
 
 // Setup / utility column FFT (not pipelined): plane src -> dst, in place
-// allowed; B columns (inside one tile) per block.
+// allowed; B columns (inside one tile) per block.  Loads and stores walk the
+// B columns fastest (coalesced rows of the tile); the in-place stages walk a
+// column's team fastest (conflict-free with the phys() padding); results are
+// read in storage (digit-reversed) order so that shared reads stay
+// conflict-free, and scattered to their rows.
 template <int M, bool INV>
 __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
                             const float2* __restrict__ tw, int B, int src_sel, int dst_sel) {
@@ -244,22 +248,24 @@ __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
   const int cpi = Lc / B;
   const ImgDesc& d = imgs[cd.img0 + blockIdx.x / cpi];
   const int c0 = (blockIdx.x % cpi) * B;
-  const int b = threadIdx.x % B, j = threadIdx.x / B;
-  const size_t off = (size_t)(c0 / TB) * M * TB + (c0 % TB) + b;
-  float2* buf = smem + b * team_stride(M);
+  const int ts = col_team_stride(M, B);
+  const int bs = threadIdx.x % B, js = threadIdx.x / B;
+  const int bf = T >= 16 ? threadIdx.x / T : bs, jf = T >= 16 ? threadIdx.x % T : js;
+  const size_t off = (size_t)(c0 / TB) * M * TB + (c0 % TB) + bs;
+  float2* bufs = smem + bs * ts;
   const float2* src = cplx_plane(d, src_sel) + off;
   float2* dst = cplx_plane(d, dst_sel) + off;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int a = j + i * T;
-    buf[phys(a)] = src[(size_t)a * TB];
+    const int a = js + i * T;
+    bufs[phys(a)] = src[(size_t)a * TB];
   }
   __syncthreads();
-  fft_team<M, INV>(buf, j, tw);
+  fft_team<M, INV>(smem + bf * ts, jf, tw + tab_off(M));
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int k = j + i * T;
-    dst[(size_t)k * TB] = buf[phys(out_pos<M>(k))];
+    const int p = js + i * T;
+    dst[(size_t)in_pos<M>(p) * TB] = bufs[phys(p)];
   }
 }
 
@@ -272,19 +278,20 @@ GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
 }
 
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
-// the first evaluation of Eq. 11 at the nodes of the image's bracket.  The S,
-// H and Y tiles of the next item land while the current one is processed
-// (S only for M = 4096, where three landing tiles do not fit).  A block
-// takes a contiguous range of items and keeps its per-node sums in registers
-// while consecutive items belong to the same image; it publishes them (one
-// partial slot, one counter update) only when the image changes.
+// the first evaluation of Eq. 11 at the nodes of the image's bracket.  Only
+// the S tile lands in shared memory; it is consumed by the first FFT stage,
+// after which the next item's tile is requested, so the copy overlaps the
+// remaining stages and the Eq. 11 sums (H and Y are read from global memory
+// in that loop).  A block takes a contiguous range of items and keeps its
+// per-node sums in registers while consecutive items belong to the same
+// image; it publishes them (one partial slot, one counter update) only when
+// the image changes.
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                  const float2* __restrict__ tw, int iter, int row_items) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
-  constexpr bool HY_LAND = M < 4096;
   __shared__ float s_nodes[KNODES];
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
@@ -296,21 +303,18 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   const int first = blockIdx.x * per_cta;
   const int stop = min(first + per_cta, n_items);
   const int tile = M * B;
+  const int ts = col_team_stride(M, B);
   float2* landS = smem;
-  float2* landH = landS + tile;
-  float2* landY = landH + tile;
-  float2* work = HY_LAND ? landY + tile : landH;
-  double* red = reinterpret_cast<double*>(work + B * team_stride(M));
+  float2* work = landS + tile;
+  double* red = reinterpret_cast<double*>(work + B * ts);
+  // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
+  const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
   auto issue = [&](int item) {
     if (item < stop) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
       issue_tile(landS, d.S + off, M, B, B);
-      if constexpr (HY_LAND) {
-        issue_tile(landH, d.H + off, M, B, B);
-        issue_tile(landY, d.Y + off, M, B, B);
-      }
     }
     cp_async_commit();
   };
@@ -368,25 +372,26 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
       block_sum_columns(d.rowsum, row_items, 1, 1, red, s_tot);
       if (threadIdx.x == 0) S->sum_u = s_tot[0];
     }
-    float2* buf = work + b * team_stride(M);
-    fft_team_from<M, false>(landS + b, StridedIdx{B}, buf, j, tw);  // ends synchronised
+    float2* buf = work + b * ts;
+    Stage0From<M, R, false>::run(landS + b, StridedIdx{B}, buf, j, tw + tab_off(M), PaddedIdx());
+    __syncthreads();  // the landing tile is consumed
+    issue(item + 1);
+    Stage<M, R, false, 1>::run(work + bf * ts, jf, tw + tab_off(M), PaddedIdx());  // ends synchronised
     float nodes[KNODES];
 #pragma unroll
     for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
     float2* spec = d.S + off + b;
+    const float2* Hc = d.H + off + b;
+    const float2* Yc = d.Y + off + b;
     if (col != 0) {
+      // positions p in storage order; p holds output row k = in_pos(p)
 #pragma unroll 4
       for (int i = 0; i < R; ++i) {
-        const int k = j + i * T;
-        float2 Hk, Yk;
-        if constexpr (HY_LAND) {
-          Hk = landH[k * B + b];
-          Yk = landY[k * B + b];
-        } else {
-          Hk = __ldg(&d.H[off + (size_t)k * B + b]);
-          Yk = __ldg(&d.Y[off + (size_t)k * B + b]);
-        }
-        const float2 U = buf[phys(out_pos<M>(k))];
+        const int p = j + i * T;
+        const int k = in_pos<M>(p);
+        const float2 Hk = __ldg(&Hc[(size_t)k * B]);
+        const float2 Yk = __ldg(&Yc[(size_t)k * B]);
+        const float2 U = buf[phys(p)];
         spec[(size_t)k * B] = U;
         const float2 r = csub(cmul(Hk, U), Yk);
         const float rr = fmaf(r.x, r.x, r.y * r.y);
@@ -420,8 +425,6 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
       }
     }
     ++count;
-    __syncthreads();      // every landing tile of this item is consumed
-    issue(item + 1);
   }
   if (count > 0) flush();
   cp_async_wait<0>();
@@ -519,41 +522,36 @@ GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool bra
   }
 }
 
-// Spectral solves fused with the inverse column FFTs: an item's U_E, H and Y
-// tiles land together (U_E only for M = 4096); Eq. 8 and 9 fill two work
-// tiles (U_I, U_p) that are inverse-transformed while the next item's tiles
-// are fetched.
+// Spectral solves fused with the inverse column FFTs: an item's U_E tile
+// lands in shared memory (H and Y are read from global memory next to it);
+// Eq. 8 and 9 fill two work tiles (U_I, U_p) that are inverse-transformed
+// while the next item's tile is fetched.
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st,
                 const float2* __restrict__ tw, const float* __restrict__ d2tab) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
-  constexpr bool HY_LAND = M < 4096;
   const int N = cd.N, Lc = N / 2, B = cd.TB;
   const int cpi = Lc / B;
   const int n_items = cd.n_img * cpi;
   const int tile = M * B;
+  const int ts = col_team_stride(M, B);
   float2* landU = smem;
-  float2* landH = landU + tile;
-  float2* landY = landH + tile;
-  float2* workI = HY_LAND ? landY + tile : landH;
-  float2* workP = workI + B * team_stride(M);
+  float2* workI = landU + tile;
+  float2* workP = workI + B * ts;
+  // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
+  const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
   auto issue = [&](int item) {
     if (item < n_items) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
       issue_tile(landU, d.S + off, M, B, B);
-      if constexpr (HY_LAND) {
-        issue_tile(landH, d.H + off, M, B, B);
-        issue_tile(landY, d.Y + off, M, B, B);
-      }
     }
     cp_async_commit();
   };
   issue(blockIdx.x);
-  const int nstep = TW_N / N;  // d2tab stride for the column frequency
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     cp_async_wait<0>();
     __syncthreads();
@@ -565,25 +563,21 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     const double lamd = __ldcg(&st[gi].lam);
     const bool branch = !(lamd < 1e300);
     const float lam = branch ? 0.0f : (float)lamd;
-    const float d2c = __ldg(&d2tab[col * nstep]);
-    float2* bufI = workI + b * team_stride(M);
-    float2* bufP = workP + b * team_stride(M);
+    const float d2c = __ldg(&d2tab[tab_off(N) + col]);
+    float2* bufI = workI + b * ts;
+    float2* bufP = workP + b * ts;
+    const float2* Hc = d.H + off + b;
+    const float2* Yc = d.Y + off + b;
 #pragma unroll 4
     for (int i = 0; i < R; ++i) {
       const int k = j + i * T;
       const int e = k * B + b;
-      const float d2r = __ldg(&d2tab[k * (TW_N / M)]);
+      const float d2r = __ldg(&d2tab[tab_off(M) + k]);
       const float2 U = landU[e];
       float2 UI, Up;
       if (col != 0) {
-        float2 Hv, Yv;
-        if constexpr (HY_LAND) {
-          Hv = landH[e];
-          Yv = landY[e];
-        } else {
-          Hv = __ldg(&d.H[off + e]);
-          Yv = __ldg(&d.Y[off + e]);
-        }
+        const float2 Hv = __ldg(&Hc[(size_t)k * B]);
+        const float2 Yv = __ldg(&Yc[(size_t)k * B]);
         solve_bin(U, Hv, Yv, lam, d2r + d2c, branch, UI, Up);
       } else {
         const float2 Um = landU[((M - k) & (M - 1)) * B + b];
@@ -599,16 +593,15 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     }
     __syncthreads();
     issue(item + gridDim.x);
-    fft_team<M, true>(bufI, j, tw);
-    fft_team<M, true>(bufP, j, tw);
+    fft_team2<M, true>(workI + bf * ts, workP + bf * ts, jf, tw + tab_off(M));
     float2* qi = d.QI + off + b;
     float2* qp = d.Qp + off + b;
-#pragma unroll
+#pragma unroll 4
     for (int i = 0; i < R; ++i) {
-      const int k = j + i * T;
-      const int p = phys(out_pos<M>(k));
-      qi[(size_t)k * B] = bufI[p];
-      qp[(size_t)k * B] = bufP[p];
+      const int p = j + i * T;  // storage order; row in_pos(p)
+      const size_t k = (size_t)in_pos<M>(p);
+      qi[k * B] = bufI[phys(p)];
+      qp[k * B] = bufP[phys(p)];
     }
   }
   cp_async_wait<0>();
@@ -754,7 +747,7 @@ static void do_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst
   if (B < 1) B = 1;
   if (B > Lc) B = Lc;
   if (B > c.cd.TB) B = c.cd.TB;  // a block stays inside one tile
-  const size_t smem = (size_t)B * team_stride(M) * sizeof(float2);
+  const size_t smem = (size_t)B * col_team_stride(M, B) * sizeof(float2);
   const int nblk = c.cd.n_img * (Lc / B);
   if (inv)
     k_col_plain<M, true><<<nblk, B * T, smem, s>>>(c.cd, c.imgs, t.tw, B, src, dst);
@@ -774,7 +767,7 @@ cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int
 template <int M>
 static size_t col_smem(int B, int landings, int works, int nthr) {
   return (size_t)landings * M * B * sizeof(float2) +
-         (size_t)works * B * team_stride(M) * sizeof(float2) +
+         (size_t)works * B * col_team_stride(M, B) * sizeof(float2) +
          (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
 }
 
@@ -782,7 +775,7 @@ template <int M>
 static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
   const int Lc = c.cd.N / 2, B = c.cd.TB;
   const int nthr = B * threads_per_team(M);
-  const size_t smem = col_smem<M>(B, M < 4096 ? 3 : 1, 1, nthr);
+  const size_t smem = col_smem<M>(B, 1, 1, nthr);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items);
   const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M);
@@ -811,7 +804,7 @@ template <int M>
 static void do_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s) {
   const int Lc = c.cd.N / 2, B = c.cd.TB;
   const int nthr = B * threads_per_team(M);
-  const size_t smem = col_smem<M>(B, M < 4096 ? 3 : 1, 2, 0);
+  const size_t smem = col_smem<M>(B, 1, 2, 0);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_solve_inv<M>, nthr, smem, n_items);
   k_col_solve_inv<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, t.d2);

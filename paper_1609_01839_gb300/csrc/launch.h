@@ -28,8 +28,8 @@ struct TileConfig {
 extern TileConfig g_tiles;
 
 struct Tables {
-  const float2* tw;   // W_4096^m
-  const float* d2;    // 4 sin^2(pi m / 4096)
+  const float2* tw;   // W_L^m for every L = 2..4096, size L at offset tab_off(L)
+  const float* d2;    // 4 sin^2(pi m / L), same layout
 };
 
 // Images of a class sharing one guided-filter radius (contiguous range).
