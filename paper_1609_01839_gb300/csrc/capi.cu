@@ -70,6 +70,7 @@ struct gfdeconv_ctx {
   gfdeconv_opts opts{};
   float2* tw = nullptr;
   float* d2 = nullptr;
+  float4* twdf = nullptr;
   cudaStream_t cap = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -297,7 +298,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
 
 cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullptr) {
   long long L = 0;
-  const Tables t{c->tw, c->d2};
+  const Tables t{c->tw, c->d2, c->twdf};
   const int plain = c->opts.var_precision == 1 ? 1 : 0;
   GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(c->d_st, 0, sizeof(ImgState) * pl.n, s));
   for (auto& cl : pl.classes) {
@@ -310,10 +311,9 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   }
   for (auto& cl : pl.classes) {
     GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
-    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_UI, SEL_S, false, s));
-    GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_H, false, s));
-    GFD_T(GFD_PHASE_SETUP, launch_row_r2c(cl, t, SEL_Y, SEL_S, false, s));
-    GFD_T(GFD_PHASE_SETUP, launch_col_plain(cl, t, SEL_S, SEL_YS, false, s));
+    // H and Y in double-float, rounded once (they fix the residual of Eq. 10-11)
+    GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_UI, SEL_H, s));
+    GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_Y, SEL_YS, s));
     GFD_T(GFD_PHASE_SETUP, launch_unpack_dc(cl, s));
     L += 6;
   }
@@ -491,7 +491,18 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
       d2[tab_off(L) + m] = (float)(4.0 * sn * sn);
     }
   }
+  std::vector<float4> twdf(TAB_ENTRIES);
+  for (int L = 2; L <= TW_N; L *= 2) {
+    for (int m = 0; m < L; ++m) {
+      const double th = 2.0 * pi * m / L;
+      const double re = std::cos(th), im = -std::sin(th);
+      const float rh = (float)re, ih = (float)im;
+      twdf[tab_off(L) + m] = make_float4(rh, (float)(re - rh), ih, (float)(im - ih));
+    }
+  }
   if ((e = cudaMalloc(&c->tw, sizeof(float2) * TAB_ENTRIES)) != cudaSuccess ||
+      (e = cudaMalloc(&c->twdf, sizeof(float4) * TAB_ENTRIES)) != cudaSuccess ||
+      (e = cudaMemcpy(c->twdf, twdf.data(), sizeof(float4) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMalloc(&c->d2, sizeof(float) * TAB_ENTRIES)) != cudaSuccess ||
       (e = cudaMemcpy(c->tw, tw.data(), sizeof(float2) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d2, d2.data(), sizeof(float) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -516,6 +527,7 @@ void gfdeconv_destroy(gfdeconv_ctx* c) {
     if (a.done) cudaEventDestroy(a.done);
   }
   if (c->tw) cudaFree(c->tw);
+  if (c->twdf) cudaFree(c->twdf);
   if (c->d2) cudaFree(c->d2);
   if (c->ws) cudaFree(c->ws);
   if (c->d_imgs) cudaFree(c->d_imgs);
@@ -742,7 +754,7 @@ int gfdeconv_fft2_r2c(gfdeconv_ctx* c, const float* x, int M, int N, float* X, v
   cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
-  const Tables t{c->tw, c->d2};
+  const Tables t{c->tw, c->d2, c->twdf};
   if ((e = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s)) != cudaSuccess) return map_err(e);
   if ((e = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s)) != cudaSuccess) return map_err(e);
   return map_err(aux_finish(a, s));
@@ -768,7 +780,7 @@ int gfdeconv_fft2_c2r(gfdeconv_ctx* c, const float* X, int M, int N, float* x, v
   cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = a->d_img;
   cl.st = c->aux_st;
-  const Tables t{c->tw, c->d2};
+  const Tables t{c->tw, c->d2, c->twdf};
   if ((e = launch_col_plain(cl, t, SEL_QI, SEL_QI, true, s)) != cudaSuccess) return map_err(e);
   if ((e = launch_row_c2r(cl, t, SEL_QI, -1, SEL_UI, -1, 1.0f / ((float)M * (float)N), s)) !=
       cudaSuccess)
@@ -847,7 +859,7 @@ int gfdeconv_fft2_r2c_noalloc(gfdeconv_ctx* c, const float* x, int M, int N, flo
   cl.cd = ClassDesc{M, N, 1, 0, N / 2};
   cl.imgs = d_desc;
   cl.st = nullptr;  // the plain passes keep no per-image state
-  const Tables t{c->tw, c->d2};
+  const Tables t{c->tw, c->d2, c->twdf};
   if ((e = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s)) != cudaSuccess) return map_err(e);
   if ((e = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s)) != cudaSuccess) return map_err(e);
   return GFD_OK;

@@ -90,6 +90,7 @@ struct ImgState {
   double sum_u;      // FP64 sum of the current iterate u_E (its DC bin)
   double d00;        // DC residual sum(h) sum(u_E) - sum(y), FP64
   double err2;       // FP64 sum (u - u_orig)^2
+  double lam_prev;   // last finite lambda resolved before the current one
   float node[KNODES];// node values lambda_j (float) of the pending pass
   unsigned int cta_done;   // items of the current spectral pass completed
   unsigned int gf_done;    // last-block-done counter (guided filter)

@@ -67,7 +67,23 @@ __device__ constexpr float kSin16[16] = {
     0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
     -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
 
-// v * W_R^k (forward: exp(-2 pi i k/R); inverse: exp(+2 pi i k/R)), R <= 16
+// The rounding residuals of kCos16 / kSin16 (value minus its float), so that
+// hi + lo carries cos and sin to about 48 bits.  With the floats alone every
+// non-trivial constant twiddle has |w| < 1 (all six round towards zero), and
+// a transform shrinks every output by ~7e-8 of its magnitude: a bias, not a
+// random error, which sums of squares of spectra (the residual of Eq. 10-11)
+// inherit in full.
+constexpr float kC1 = 2.830748968563057e-08f;   // cos(pi/8) residual
+constexpr float kS1 = 6.2233507236442165e-09f;  // sin(pi/8) residual
+constexpr float kC2 = 1.2101617485882343e-08f;  // cos(pi/4) residual
+__device__ constexpr float kCos16Lo[16] = {0.0f, kC1,  kC2,  kS1,  0.0f, -kS1, -kC2, -kC1,
+                                           0.0f, -kC1, -kC2, -kS1, 0.0f, kS1,  kC2,  kC1};
+__device__ constexpr float kSin16Lo[16] = {0.0f, kS1,  kC2,  kC1,  0.0f, kC1,  kC2,  kS1,
+                                           0.0f, -kS1, -kC2, -kC1, 0.0f, -kC1, -kC2, -kS1};
+
+// v * W_R^k (forward: exp(-2 pi i k/R); inverse: exp(+2 pi i k/R)), R <= 16.
+// The product uses the constants' residuals (two more FMAs per component), so
+// it is the exact product up to roundings of either sign.
 template <int R, int k, bool INV>
 GFD_D float2 const_twiddle(float2 v) {
   if constexpr (k == 0) {
@@ -76,9 +92,11 @@ GFD_D float2 const_twiddle(float2 v) {
     return cmul_mi<INV>(v);
   } else {
     constexpr int m = k * (16 / R);
-    const float c = kCos16[m];
+    const float c = kCos16[m], cl = kCos16Lo[m];
     const float s = INV ? kSin16[m] : -kSin16[m];
-    return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+    const float sl = INV ? kSin16Lo[m] : -kSin16Lo[m];
+    return make_float2(fmaf(v.x, c, fmaf(-v.y, s, fmaf(v.x, cl, -v.y * sl))),
+                       fmaf(v.x, s, fmaf(v.y, c, fmaf(v.x, sl, v.y * cl))));
   }
 }
 

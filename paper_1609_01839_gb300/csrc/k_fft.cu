@@ -295,6 +295,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   __shared__ float s_nodes[KNODES];
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
+  __shared__ WarpAcc s_wacc;
   const int B = cd.TB;
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
@@ -328,7 +329,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   auto flush = [&]() {
     ImgState* S = st + cur;
     const ImgDesc& d = imgs[cur];
-    block_partials(acc, red, d.part + (size_t)slot * (KNODES + 1));
+    block_partials_folded(&s_wacc, d.part + (size_t)slot * (KNODES + 1));
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -348,10 +349,9 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         __threadfence();
       }
     }
-#pragma unroll
-    for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
     count = 0;
   };
+  warp_acc_clear(&s_wacc);  // first use follows the loop's __syncthreads()
   issue(first);
   for (int item = first; item < stop; ++item) {
     cp_async_wait<0>();
@@ -424,6 +424,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         spec[(size_t)k * B] = U;
       }
     }
+    warp_fold(acc, &s_wacc);
     ++count;
   }
   if (count > 0) flush();
@@ -440,6 +441,7 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
   __shared__ double red[32 * (KNODES + 1)];
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
+  __shared__ WarpAcc s_wacc;
   const int Lc = cd.N / 2, TB = cd.TB, M = cd.M;
   const int per_img = M * Lc;
   const int cpi = per_img / chunk;
@@ -448,6 +450,7 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
   if (__ldcg(&S->need) == 0) return;
   const ImgDesc& d = imgs[gi];
   for (int q = threadIdx.x; q < KNODES; q += blockDim.x) s_nodes[q] = __ldcg(&S->node[q]);
+  warp_acc_clear(&s_wacc);
   __syncthreads();
   float nodes[KNODES];
 #pragma unroll
@@ -456,10 +459,14 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
 #pragma unroll
   for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
   const int e0 = (blockIdx.x % cpi) * chunk;
-  const int tile = M * TB;
-  for (int e = e0 + threadIdx.x; e < e0 + chunk; e += blockDim.x) {
-    const int t = e / tile, rem = e - t * tile;
-    const int k = rem / TB, b = rem - k * TB;
+  const int lg_tile = __ffs(M * TB) - 1, lg_tb = __ffs(TB) - 1;  // powers of two
+  // runs of 16 bins per thread between folds (uniform control flow)
+  for (int base = e0; base < e0 + chunk; base += 16 * blockDim.x) {
+   for (int q = 0; q < 16; ++q) {
+    const int e = base + q * blockDim.x + threadIdx.x;
+    if (e >= e0 + chunk) break;
+    const int t = e >> lg_tile, rem = e & ((1 << lg_tile) - 1);
+    const int k = rem >> lg_tb, b = rem & (TB - 1);
     const int col = t * TB + b;
     const float2 U = d.S[e];
     if (col != 0) {
@@ -483,8 +490,10 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
       accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
       accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
     }
+   }
+   warp_fold(acc, &s_wacc);
   }
-  block_partials(acc, red, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
+  block_partials_folded(&s_wacc, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
   if (last_item(&S->cta_done, cpi, &s_flag)) {
     block_sum_columns(d.part, cpi, KNODES + 1, KNODES + 1, red, s_tot);
     for (int q = threadIdx.x; q < cpi * (KNODES + 1); q += blockDim.x) d.part[q] = 0.0;
@@ -794,7 +803,7 @@ cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int ite
 cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
                                cudaStream_t s) {
   const int per_img = c.cd.M * (c.cd.N / 2);
-  const int chunk = per_img < 4096 ? per_img : 4096;
+  const int chunk = per_img < 16384 ? per_img : 16384;
   const int nblk = c.cd.n_img * (per_img / chunk);
   k_lambda_pass<<<nblk, 256, 0, s>>>(c.cd, c.imgs, c.st, chunk, iter, last_chance ? 1 : 0);
   return cudaGetLastError();

@@ -1,0 +1,218 @@
+// Double-float 2-D real DFT for the once-per-solve spectra H = F(h) and
+// Y = F(y) (Sec. 3.1: the solves of Eq. 8-9 and the residual of Eq. 10-11
+// are formed in the DFT domain).
+//
+// Why not the FP32 transform: its error is about 1e-7 of the spectrum's
+// norm in every bin, and the norm of Y is dominated by the image's mean and
+// low frequencies.  The bins that decide lambda (|H|^2 <~ lambda: high
+// frequencies, where |Y| is at the noise level) then carry errors of
+// ~1e-7 * ||y|| / sigma relative to their own size, and the root of Eq. 11
+// moves by that times its condition number.  Computing H and Y in
+// double-float arithmetic (about 48 bits, FP32 instructions only) and
+// rounding once to FP32 removes this term; the per-iteration transforms of
+// u_E stay in FP32 (their errors enter Eq. 11 multiplied by |H|).
+//
+// Same layout as the FP32 path: rows of N reals are transformed as N/2
+// complex points z[n] = x[2n] + i x[2n+1] and post-processed into the packed
+// half spectrum (X[0] + i X[N/2] in column 0), stored column-tiled; the
+// column pass transforms each packed column (length M).  Radix-2
+// decimation in time from bit-reversed order, in shared memory.
+#include "df.cuh"
+#include "launch.h"
+
+namespace gfd {
+
+struct cdf {
+  df re, im;
+};
+
+// Double-float sum with one two-sum: error within ~2^-44 (|a| + |b|).  A
+// transform needs errors small against the norm of its data, not relative
+// accuracy under cancellation, so the cheaper form suffices here.
+GFD_D df dfs_add(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+GFD_D df dfs_sub(df a, df b) { return dfs_add(a, df_neg(b)); }
+
+GFD_D cdf cdf_add(cdf a, cdf b) { return cdf{dfs_add(a.re, b.re), dfs_add(a.im, b.im)}; }
+GFD_D cdf cdf_sub(cdf a, cdf b) { return cdf{dfs_sub(a.re, b.re), dfs_sub(a.im, b.im)}; }
+GFD_D cdf cdf_mul(cdf a, cdf b) {
+  return cdf{dfs_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
+             dfs_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+GFD_D cdf cdf_half(cdf a) {  // exact
+  return cdf{df{0.5f * a.re.hi, 0.5f * a.re.lo}, df{0.5f * a.im.hi, 0.5f * a.im.lo}};
+}
+
+// W_L^m from the per-length table (float4: re hi, re lo, im hi, im lo)
+GFD_D cdf tw_df(const float4* __restrict__ tab, int L, int m) {
+  const float4 v = __ldg(&tab[tab_off(L) + m]);
+  return cdf{df{v.x, v.y}, df{v.z, v.w}};
+}
+
+// Shared buffer of one transform: hi and lo planes of re and im.
+struct CdfBuf {
+  float* rh;
+  float* rl;
+  float* ih;
+  float* il;
+  GFD_D cdf get(int i) const { return cdf{df{rh[i], rl[i]}, df{ih[i], il[i]}}; }
+  GFD_D void put(int i, cdf v) const {
+    rh[i] = v.re.hi;
+    rl[i] = v.re.lo;
+    ih[i] = v.im.hi;
+    il[i] = v.im.lo;
+  }
+};
+
+// In-place radix-2 DIT transform of length L (input already bit-reversed)
+// by `nt` threads with index t; synchronises the block after every stage.
+GFD_D void fft_df(const CdfBuf& x, int L, const float4* __restrict__ tab, int t, int nt) {
+  for (int half = 1; half < L; half <<= 1) {
+    const int step = L / (2 * half);  // W_{2 half}^j = W_L^(j * step)
+    for (int b = t; b < L / 2; b += nt) {
+      const int j = b & (half - 1);
+      const int k = ((b - j) << 1) + j;
+      const cdf w = tw_df(tab, L, j * step);
+      const cdf u = x.get(k);
+      const cdf v = cdf_mul(w, x.get(k + half));
+      x.put(k, cdf_add(u, v));
+      x.put(k + half, cdf_sub(u, v));
+    }
+    __syncthreads();
+  }
+}
+
+GFD_D int bitrev(int i, int lg) { return (int)(__brev((unsigned)i) >> (32 - lg)); }
+
+// Row pass: real plane src -> packed row spectra, hi to plane dhi, lo to
+// plane dlo (tiled layout).  One block per row.
+__global__ void __launch_bounds__(256)
+k_row_r2c_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __restrict__ tab,
+             int src_sel, int dhi_sel, int dlo_sel) {
+  extern __shared__ float sm[];
+  const int M = cd.M, N = cd.N, L = N / 2, TB = cd.TB;
+  const int li = blockIdx.x / M, row = blockIdx.x - li * M;
+  const ImgDesc& d = imgs[cd.img0 + li];
+  const CdfBuf x{sm, sm + L, sm + 2 * L, sm + 3 * L};
+  const int lg = __ffs(L) - 1;
+  const float* src = (src_sel == SEL_Y ? d.y : (src_sel == SEL_UI ? d.uI : d.u)) + (size_t)row * N;
+  for (int n = threadIdx.x; n < L; n += blockDim.x) {
+    const float2 v = *reinterpret_cast<const float2*>(src + 2 * n);
+    x.put(L == 1 ? 0 : bitrev(n, lg), cdf{df{v.x, 0.0f}, df{v.y, 0.0f}});
+  }
+  __syncthreads();
+  fft_df(x, L, tab, threadIdx.x, blockDim.x);
+  float2* dhi = reinterpret_cast<float2*>(dhi_sel == SEL_S ? d.S : d.QI);
+  float2* dlo = reinterpret_cast<float2*>(dlo_sel == SEL_S ? d.S : d.QI);
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const cdf Zk = x.get(k);
+    cdf X;
+    if (k == 0) {
+      X = cdf{dfs_add(Zk.re, Zk.im), dfs_sub(Zk.re, Zk.im)};  // X[0] + i X[N/2]
+    } else {
+      const cdf Zm0 = x.get(L - k);
+      const cdf Zm = cdf{Zm0.re, df_neg(Zm0.im)};  // conj Z[L-k]
+      const cdf E = cdf_half(cdf_add(Zk, Zm));
+      const cdf D = cdf_half(cdf_sub(Zk, Zm));
+      const cdf O = cdf{D.im, df_neg(D.re)};  // (Zk - Zm) / (2i)
+      X = cdf_add(E, cdf_mul(tw_df(tab, N, k), O));
+    }
+    const size_t o = (size_t)(k / TB) * M * TB + (size_t)row * TB + (k % TB);
+    dhi[o] = make_float2(X.re.hi, X.im.hi);
+    dlo[o] = make_float2(X.re.lo, X.im.lo);
+  }
+}
+
+// Column pass: packed rows (hi in plane shi, lo in plane slo) -> complex
+// column transforms rounded once into plane dst.  One block per tile of TB
+// columns; threads split over the tile's columns.
+__global__ void __launch_bounds__(512)
+k_col_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __restrict__ tab,
+         int shi_sel, int slo_sel, int dst_sel) {
+  extern __shared__ float sm[];
+  const int M = cd.M, L = cd.N / 2, TB = cd.TB;
+  const int tiles = L / TB;
+  const int li = blockIdx.x / tiles, t = blockIdx.x - li * tiles;
+  const ImgDesc& d = imgs[cd.img0 + li];
+  const int lg = __ffs(M) - 1;
+  const size_t off = (size_t)t * M * TB;
+  const float2* shi = reinterpret_cast<const float2*>(shi_sel == SEL_S ? d.S : d.QI) + off;
+  const float2* slo = reinterpret_cast<const float2*>(slo_sel == SEL_S ? d.S : d.QI) + off;
+  float2* dst = reinterpret_cast<float2*>(dst_sel == SEL_H ? d.H : d.Y) + off;
+  for (int e = threadIdx.x; e < M * TB; e += blockDim.x) {
+    const int m = e / TB, b = e - m * TB;
+    const float2 h = shi[e], l = slo[e];
+    const CdfBuf x{sm + b * 4 * M, sm + b * 4 * M + M, sm + b * 4 * M + 2 * M, sm + b * 4 * M + 3 * M};
+    x.put(M == 1 ? 0 : bitrev(m, lg), cdf{df{h.x, l.x}, df{h.y, l.y}});
+  }
+  __syncthreads();
+  // threads per column: the block's threads split evenly over the TB columns
+  const int per = blockDim.x / TB;
+  const int b = threadIdx.x / per, tt = threadIdx.x - b * per;
+  const CdfBuf x{sm + b * 4 * M, sm + b * 4 * M + M, sm + b * 4 * M + 2 * M, sm + b * 4 * M + 3 * M};
+  for (int half = 1; half < M; half <<= 1) {
+    const int step = M / (2 * half);
+    if (b < TB) {
+      for (int q = tt; q < M / 2; q += per) {
+        const int j = q & (half - 1);
+        const int k = ((q - j) << 1) + j;
+        const cdf w = tw_df(tab, M, j * step);
+        const cdf u = x.get(k);
+        const cdf v = cdf_mul(w, x.get(k + half));
+        x.put(k, cdf_add(u, v));
+        x.put(k + half, cdf_sub(u, v));
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < M * TB; e += blockDim.x) {
+    const int m = e / TB, bb = e - m * TB;
+    const CdfBuf y{sm + bb * 4 * M, sm + bb * 4 * M + M, sm + bb * 4 * M + 2 * M,
+                   sm + bb * 4 * M + 3 * M};
+    const cdf v = y.get(m);
+    dst[e] = make_float2(v.re.hi + v.re.lo, v.im.hi + v.im.lo);
+  }
+}
+
+static int df_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Precise 2-D real DFT of real plane src into spectrum plane dst (SEL_H or
+// SEL_YS), using the S and Q_I planes as the double-float intermediate.
+cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* tab, int src, int dst,
+                               cudaStream_t s) {
+  (void)df_sm_count;
+  const int M = c.cd.M, L = c.cd.N / 2, TB = c.cd.TB;
+  const int rthreads = L / 2 < 256 ? (L / 2 < 32 ? 32 : L / 2) : 256;
+  k_row_r2c_df<<<c.cd.n_img * M, rthreads, (size_t)4 * L * sizeof(float), s>>>(
+      c.cd, c.imgs, tab, src, SEL_S, SEL_QI);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int per = M / 2 < 64 ? M / 2 : 64;
+  if (per < 1) per = 1;
+  int cthreads = per * TB;
+  if (cthreads > 512) cthreads = 512 - 512 % TB;
+  if (cthreads < TB) cthreads = TB;
+  const size_t smem = (size_t)TB * 4 * M * sizeof(float);
+  k_col_df<<<c.cd.n_img * (L / TB), cthreads, smem, s>>>(c.cd, c.imgs, tab, SEL_S, SEL_QI,
+                                                        dst == SEL_H ? SEL_H : SEL_YS);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_df_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_col_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       160 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_row_r2c_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+}
+
+}  // namespace gfd

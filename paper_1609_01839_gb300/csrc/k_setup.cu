@@ -193,10 +193,12 @@ cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s) {
 
 cudaError_t configure_fft_kernels();
 cudaError_t configure_gf_kernel();
+cudaError_t configure_df_kernels();
 
 cudaError_t configure_kernels() {
   cudaError_t e = configure_fft_kernels();
   if (e != cudaSuccess) return e;
+  if ((e = configure_df_kernels()) != cudaSuccess) return e;
   return configure_gf_kernel();
 }
 

@@ -73,11 +73,20 @@ GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane) {
 }
 
 // One bin's contribution: wr = (Hermitian weight) * r, a = |H|^2.
+// t = lambda / (a + lambda) comes from an approximate reciprocal refined by
+// one FMA residual step, which makes it (almost always) the correctly
+// rounded quotient.  Without the step, every bin with a << lambda would carry
+// the same reciprocal error for a given node: a node-dependent bias of ~1e-7
+// in f(lambda_j) that moves the root by ~1e-7 / |d ln f / d ln lambda|,
+// i.e. by percents where f is nearly flat in lambda.
 GFD_D void accum_bin(float wr, float a, const float* nodes, float* acc) {
   acc[KNODES] += wr;
 #pragma unroll
   for (int j = 0; j < KNODES; ++j) {
-    const float t = __fdividef(nodes[j], a + nodes[j]);
+    const float d = a + nodes[j];
+    const float q = __fdividef(1.0f, d);
+    const float t0 = nodes[j] * q;
+    const float t = fmaf(fmaf(-t0, d, nodes[j]), q, t0);
     acc[j] = fmaf(wr, t * t, acc[j]);
   }
 }
@@ -100,6 +109,55 @@ GFD_D void block_partials(float* acc, double* red, double* part) {
     part[j] = s;
   }
   __syncthreads();
+}
+
+// Long sums of the per-bin terms.  Threads keep FP32 partials over a short
+// run of bins (one item); warp_fold adds the warp's total of each partial to
+// per-warp double-float accumulators in shared memory (hi + lo, exact
+// two-sum) and clears the partials; block_partials_folded turns the per-warp
+// accumulators into the block's FP64 sums.  This keeps f(lambda) and
+// ||h*u_E - y||^2 accurate to about 1e-10 relative over millions of bins,
+// which matters where f is nearly flat in lambda.
+struct WarpAcc {
+  float hi[16][KNODES + 1];
+  float lo[16][KNODES + 1];
+};
+
+GFD_D void warp_fold(float* acc, WarpAcc* wa) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j <= KNODES; ++j) {
+    const float v = warp_sum(acc[j]);
+    if (lane == 0) {
+      const df t = two_sum(wa->hi[warp][j], v);
+      wa->hi[warp][j] = t.hi;
+      wa->lo[warp][j] += t.lo;
+    }
+    acc[j] = 0.0f;
+  }
+}
+
+// part[j] = sum over warps of hi + lo (FP64); clears the accumulators.
+// Synchronises before and after.
+GFD_D void block_partials_folded(WarpAcc* wa, double* part) {
+  __syncthreads();
+  const int nwarp = num_warps();
+  for (int j = threadIdx.x; j <= KNODES; j += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nwarp; ++w) {
+      s += (double)wa->hi[w][j] + (double)wa->lo[w][j];
+      wa->hi[w][j] = 0.0f;
+      wa->lo[w][j] = 0.0f;
+    }
+    part[j] = s;
+  }
+  __syncthreads();
+}
+
+// Zero the accumulators (every thread calls; synchronise before use).
+GFD_D void warp_acc_clear(WarpAcc* wa) {
+  float* p = &wa->hi[0][0];
+  for (int i = threadIdx.x; i < 2 * 16 * (KNODES + 1); i += blockDim.x) p[i] = 0.0f;
 }
 
 GFD_D double warp_sum_dbl(double v) {
@@ -214,14 +272,39 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
   return 0.5 * (df_to_double(a) + df_to_double(b));
 }
 
+// Record lambda_k and set the bracket of iteration k+1's fused first pass.
+// lambda jumps by a factor of 2..150 from the first iteration (u_E = 0) to
+// the second and by 1/8..8 to the third; later it changes smoothly, so the
+// bracket is centred on the extrapolation lambda_k (lambda_k / lambda_{k-1})
+// (ratio clamped to [1/2, 2]).  The first two use geometric nodes, resolved by
+// one more pass; the later ones are narrow enough (ratio 1.5625) for the
+// interpolation to resolve them in the fused pass itself.
 GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int lane) {
   if (lane == 0) {
     st->lam = lam;
     st->need = 0;
     if (lam_out) lam_out[iter] = lam;
   }
-  if (isfinite(lam) && lam > 0.0)
-    set_bracket_warp(st, (float)(lam / PRIMARY_RATIO), (float)(lam * PRIMARY_RATIO), lane);
+  if (isfinite(lam) && lam > 0.0) {
+    const float l = (float)lam;
+    float lo, hi;
+    if (iter == 0) {
+      lo = l;
+      hi = 150.0f * l;
+    } else if (iter == 1) {
+      lo = 0.125f * l;
+      hi = 8.0f * l;
+    } else {
+      const double prev = st->lam_prev;
+      float c = l;
+      if (isfinite(prev) && prev > 0.0) c = l * fminf(fmaxf((float)(lam / prev), 0.5f), 2.0f);
+      lo = c / PRIMARY_RATIO;
+      hi = c * PRIMARY_RATIO;
+    }
+    lo = fmaxf(lo, (float)LAMBDA_LO);
+    set_bracket_warp(st, lo, hi, lane);  // ends with __syncwarp()
+    if (lane == 0) st->lam_prev = lam;
+  }
   __syncwarp();
 }
 

@@ -28,8 +28,9 @@ struct TileConfig {
 extern TileConfig g_tiles;
 
 struct Tables {
-  const float2* tw;   // W_L^m for every L = 2..4096, size L at offset tab_off(L)
-  const float* d2;    // 4 sin^2(pi m / L), same layout
+  const float2* tw;    // W_L^m for every L = 2..4096, size L at offset tab_off(L)
+  const float* d2;     // 4 sin^2(pi m / L), same layout
+  const float4* twdf;  // W_L^m in double-float (re hi, re lo, im hi, im lo), same layout
 };
 
 // Images of a class sharing one guided-filter radius (contiguous range).
@@ -71,6 +72,10 @@ cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStre
 // Guided filter (Eq. 3-5): real planes (uI, up) -> u.  iter < 0: no ISNR.
 cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var,
                                  cudaStream_t s);
+// Double-float 2-D real DFT of real plane src into spectrum plane dst
+// (SEL_H or SEL_YS); uses the S and Q_I planes as scratch.
+cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* twdf, int src, int dst,
+                               cudaStream_t s);
 // Setup kernels.
 cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s);
 cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s);

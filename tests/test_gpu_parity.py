@@ -183,6 +183,56 @@ def test_teacher_forced_step_c1(ctx, c1_trace, k):
     assert np.abs(u - ref["u"]).max() < U_TOL
 
 
+def lambda_condition(p, uE, lam):
+    """kappa = 1 / |d ln f / d ln lambda| at the root of Eq. 11 (FP64)."""
+    M, N = p.shape
+    H = O.psf_spectrum(p.h, M, N)
+    UE = np.fft.fft2(uE.astype(np.float32).astype(np.float64))
+    Y = np.fft.fft2(p.y.astype(np.float64))
+    a, r = np.abs(H) ** 2, np.abs(H * UE - Y) ** 2
+    fp, fm = O.f_lambda(lam * 1.001, a, r, M * N), O.f_lambda(lam / 1.001, a, r, M * N)
+    return 1.0 / abs((math.log(fp) - math.log(fm)) / (2 * math.log(1.001)))
+
+
+# Bound on the relative error of the GPU's f(lambda_j) = (1/P) sum over bins
+# of lambda_j^2 r / (a + lambda_j)^2.  H and Y come from a double-float
+# transform (rounded once), the sums are double-float / FP64; what remains is
+# the FP32 transform of u_E in every iteration, whose rounding leaves f off by
+# ~2e-9 relative at most on the workloads tested (the errors of single bins
+# average out; a small systematic part does not).  The root then moves by
+# about kappa times that, kappa = 1 / |d ln f / d ln lambda|.
+F_REL_ERR = 1e-8
+
+
+@pytest.fixture(scope="module")
+def c2_118_trace():
+    """A heavily blurred canvas (25x25 Gaussian, sigma 2.7, BSNR 30) whose
+    discrepancy function is nearly flat in lambda from the fifth iteration on
+    (d ln f / d ln lambda ~ 3e-6): almost every bin has |H|^2 << lambda."""
+    p = S.config_c2_image(118, iters=9)
+    return p, O.solve(p.y, p.h, p.sigma, p.w, p.eps, 9, trace=True)
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_teacher_forced_step_ill_conditioned_lambda(ctx, c2_118_trace, k):
+    """lambda within kappa * F_REL_ERR (and never worse than 1e-6 where the
+    root is well conditioned); u, u_I, u_p within 2e-5 regardless: the
+    solves depend on lambda only through the bins with |H|^2 ~ lambda."""
+    p, tr = c2_118_trace
+    lam, res, u, uI, up = gpu_step(ctx, p, tr["uE"][k])
+    ref = oracle_step(p, tr["uE"][k])
+    kappa = lambda_condition(p, tr["uE"][k], ref["lam"])
+    tol = max(LAM_TOL_TF, kappa * F_REL_ERR)
+    record(f"teacher_forced_c2_118_k{k}", lam_rel=abs(lam / ref["lam"] - 1), kappa=kappa,
+           res_rel=abs(res / ref["res"] - 1), u_max_abs=np.abs(u - ref["u"]).max(),
+           uI_max_abs=np.abs(uI - ref["uI"]).max(), up_max_abs=np.abs(up - ref["up"]).max())
+    assert res == pytest.approx(ref["res"], rel=RES_TOL)
+    assert abs(lam / ref["lam"] - 1) < tol, (lam, ref["lam"], kappa)
+    assert np.abs(uI - ref["uI"]).max() < U_TOL
+    assert np.abs(up - ref["up"]).max() < U_TOL
+    assert np.abs(u - ref["u"]).max() < U_TOL
+
+
 # ---------------------------------------------------------------------------
 # Free trajectories of the whole method (Steps 0-3)
 # ---------------------------------------------------------------------------
