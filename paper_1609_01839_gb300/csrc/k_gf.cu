@@ -1,364 +1,287 @@
 // Guided filter u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5) with
-// periodic windows, streamed down column strips.
+// periodic windows, r = (w-1)/2.
 //
-// A work item is a strip of GF_W output columns and H output rows of one
-// image.  With r = (w-1)/2 the block streams the H + 4r input rows of the
-// strip's input columns (periodic wrap; 16-byte copies of a window that
-// starts on a 4-column boundary) through a ring buffer in shared memory,
-// GF_RB rows per batch, the next batch being copied asynchronously while the
-// current one is processed:
-//   1. window sums down each column of J = I - c_I, Q = p - c_p, J^2, J Q;
-//   2. window sums along each row of those -> mu_k, pbar_k, sigma_k^2 and
-//      the covariance -> a_k (Eq. 3), b_k (Eq. 4), into a ring of (a, b) rows;
-//   3. window sums of a and b down each column;
-//   4. window sums along each row -> abar, bbar -> u = abar I + bbar (Eq. 5).
-// Column sums are formed directly for the first row of each GF_SB-row
-// sub-block and slid over the rest (so every stage keeps all threads busy
-// and no sum is carried over more than GF_SB - 1 slides); row sums slide over
-// runs of GF_C columns.  Window statistics are taken about reference values
-// (c_I, c_p: the item's centre pixel), which removes the cancellation in
-// sigma_k^2 = E[I^2] - mu^2 where the window mean is close to c_I.  Images
-// narrower than GF_W are covered by one strip whose columns wrap; only the
-// first N outputs are stored.
+// Every warp works alone, down a strip of GFW_COLS input columns (4 per
+// lane): no block barriers.  Input rows enter a per-warp ring in shared
+// memory by 16-byte asynchronous copies one row ahead of use; each lane
+// copies and reads only its own 4 columns.  For the item's rows the warp
+// forms, row by row,
+//   1. window sums down its columns of J = I - c_I, Q = p - c_p, J^2, J Q
+//      (in registers; re-formed directly every GFW_SUB rows and slid in
+//      between, so no sum is carried over more than GFW_SUB - 1 slides),
+//   2. window sums along the row by warp shuffles (the 2r neighbouring
+//      columns come from the adjacent lanes) -> mu_k, pbar_k, sigma_k^2 and
+//      the covariance -> a_k (Eq. 3), b_k (Eq. 4) for each column,
+//   3. window sums of a and b down the columns (a per-warp ring of the last
+//      2r+1 rows of a, b in shared memory, each lane touching only its own
+//      columns), re-formed / slid like 1.,
+//   4. window sums along the row by shuffles -> abar, bbar ->
+//      u = abar I + bbar (Eq. 5), stored as 16-byte vectors.
+// The strip's outer 4*ceil(r/2) columns on each side are halo (their sums
+// are incomplete); the columns in between are the item's output, so
+// neighbouring strips overlap by the halo.  Input rows and columns wrap
+// periodically.  Window statistics are taken about reference values (c_I,
+// c_p: the item's centre pixel), which removes the cancellation in
+// sigma_k^2 = E[I^2] - mu^2 where the window mean is close to c_I.
 #include "common.cuh"
 #include "launch.h"
 
 namespace gfd {
 
-constexpr int GF_W = 64;       // output columns per item
-constexpr int GF_H = 128;      // output rows per item (at most M)
-constexpr int GF_RB = 16;      // input rows per batch
-constexpr int GF_SB = 4;       // rows per column-sum sub-block
-constexpr int GF_C = 4;        // columns per thread in the row sums
-constexpr int GF_THREADS = 256;
-constexpr int GF_RMAX = 8;     // w <= 17
+constexpr int GFW_COLS = 128;   // input columns per strip (4 per lane)
+constexpr int GFW_SUB = 8;      // rows between direct re-formations of the column sums
+constexpr int GFW_WARPS = 4;    // warps per block
+constexpr int GF_RMAX = 8;      // w <= 17
+constexpr unsigned FULL = 0xffffffffu;
 
-// Shared-memory geometry for window radius RAD.  Input rows hold the
-// 4-aligned column window [x0 - 4Q, x0 + GF_W + 4Q) (pitch a multiple of 4
-// for the 16-byte copies); logical column c (window start x0 - 2r) sits at
-// c + OFF.  Rows of the sums have odd pitches.
 template <int RAD>
-struct GfGeom {
+struct GfwGeom {
   static constexpr int WIN = 2 * RAD + 1;
-  static constexpr int Q = (2 * RAD + 3) / 4;
-  static constexpr int OFF = 4 * Q - 2 * RAD;
-  static constexpr int WW = GF_W + 8 * Q;          // copied input columns
-  static constexpr int CW = WW / 4;                // 16-byte chunks per row
-  static constexpr int IP = WW + 4;                // input pitch
-  static constexpr int WU = GF_W + 4 * RAD;        // columns of the statistics
-  static constexpr int W1 = GF_W + 2 * RAD;        // columns of a, b
-  static constexpr int VP = WU | 1;                // pitch of the column sums
-  static constexpr int AP = W1 | 1;                // pitch of a, b and their sums
-  static constexpr int Rin = 2 * GF_RB + 2 * RAD;  // input ring rows
-  static constexpr int Rab = GF_RB + 2 * RAD;      // a, b ring rows
-  static constexpr int floats = 2 * Rin * IP + 4 * GF_RB * VP + 2 * Rab * AP + 2 * GF_RB * AP;
+  static constexpr int RI = WIN + 2;  // input ring rows: window, the row leaving, the next
+  static constexpr int HALO = 4 * ((RAD + 1) / 2);  // >= 2r, multiple of 4
+  static constexpr int WOUT = GFW_COLS - 2 * HALO;  // output columns per strip
 };
 
-static size_t gf_smem_bytes(int rad) {
-  switch (rad) {
-    case 0: return GfGeom<0>::floats * sizeof(float);
-    case 1: return GfGeom<1>::floats * sizeof(float);
-    case 2: return GfGeom<2>::floats * sizeof(float);
-    case 3: return GfGeom<3>::floats * sizeof(float);
-    case 4: return GfGeom<4>::floats * sizeof(float);
-    case 5: return GfGeom<5>::floats * sizeof(float);
-    case 6: return GfGeom<6>::floats * sizeof(float);
-    case 7: return GfGeom<7>::floats * sizeof(float);
-    default: return GfGeom<8>::floats * sizeof(float);
-  }
-}
+// per-warp shared memory: (a, b) ring of 2r+1 rows, (I, p) ring of 2r+3 rows
+GFD_HD int gfw_ring_floats(int rad) { return (2 * (2 * rad + 1) + 2 * (2 * rad + 3)) * GFW_COLS; }
+static int gfw_wout(int rad) { return GFW_COLS - 8 * ((rad + 1) / 2); }
 
-GFD_D int wrap_dec(int s, int R) { return s == 0 ? R - 1 : s - 1; }
-GFD_D int wrap_inc(int s, int R) { return s == R - 1 ? 0 : s + 1; }
-GFD_D int wrap_sub(int s, int k, int R) {  // (s - k) mod R for 0 <= k <= R
-  const int t = s - k;
-  return t < 0 ? t + R : t;
+// Window sums of radius RAD along the strip: v[k] is column 4*lane + k;
+// s[k] = sum of columns 4*lane + k - RAD .. 4*lane + k + RAD.  Columns beyond
+// the warp's edges are not available: the lanes within RAD columns of an
+// edge get incomplete sums (those columns are halo).
+template <int RAD>
+GFD_D void hsum4(const float (&v)[4], float (&s)[4]) {
+  constexpr int E = 2 * RAD + 4;
+  float e[E];  // columns 4*lane - RAD .. 4*lane + 3 + RAD
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int c = q - RAD;                           // column offset from 4*lane
+    const int lo = c >= 0 ? c / 4 : -((3 - c) / 4);  // floor(c / 4): source lane offset
+    const int idx = c - 4 * lo;                      // column within the source lane
+    if (lo == 0)
+      e[q] = v[idx];
+    else if (lo > 0)
+      e[q] = __shfl_down_sync(FULL, v[idx], lo);
+    else
+      e[q] = __shfl_up_sync(FULL, v[idx], -lo);
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int q = 0; q <= 2 * RAD; ++q) acc += e[q];
+  s[0] = acc;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    acc += e[k + 2 * RAD] - e[k - 1];
+    s[k] = acc;
+  }
 }
 
 template <int RAD>
-GFD_D void gf_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
-                    bool shifted, int H, float* sm, double* red, int* s_flag) {
-  using G = GfGeom<RAD>;
-  constexpr int WIN = G::WIN, OFF = G::OFF, IP = G::IP, VP = G::VP, AP = G::AP;
-  constexpr int WU = G::WU, W1 = G::W1, Rin = G::Rin, Rab = G::Rab;
-  constexpr int NSB = GF_RB / GF_SB;
-  float* const inI = sm;                      // [Rin][IP]
-  float* const inP = inI + Rin * IP;          // [Rin][IP]
-  float* const vs = inP + Rin * IP;           // [4][GF_RB][VP]
-  float* const abA = vs + 4 * GF_RB * VP;     // [Rab][AP]
-  float* const abB = abA + Rab * AP;          // [Rab][AP]
-  float* const vsA = abB + Rab * AP;          // [GF_RB][AP]
-  float* const vsB = vsA + GF_RB * AP;        // [GF_RB][AP]
-  constexpr int PS = GF_RB * VP;
-
+GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgState* st,
+                     int iter, bool shifted, int H, float* ring, int gwarp, int nwarps) {
+  using G = GfwGeom<RAD>;
+  constexpr int WIN = G::WIN, HALO = G::HALO, WOUT = G::WOUT, RI = G::RI;
+  const int lane = threadIdx.x & 31;
   const int M = cd.M, N = cd.N;
-  const int tid = threadIdx.x;
-  const int strips = N >= GF_W ? N / GF_W : 1;
-  const int blocks = M / H;
-  const int per_img = strips * blocks;
+  const int strips = (N + WOUT - 1) / WOUT;
+  const int per_img = strips * (M / H);
   const int n_items = cd.n_img * per_img;
-  const int nrows = H + 4 * RAD;  // input rows of an item
-  const int nq = (nrows + GF_RB - 1) / GF_RB;
   const float inv_n = 1.0f / (float)(WIN * WIN);
+  float* const ra = ring;                   // [WIN][GFW_COLS] a
+  float* const rb = ra + WIN * GFW_COLS;    // [WIN][GFW_COLS] b
+  float* const rI = rb + WIN * GFW_COLS;    // [RI][GFW_COLS] I
+  float* const rP = rI + RI * GFW_COLS;     // [RI][GFW_COLS] p
+  // this lane's columns lie in the strip's output part
+  const bool out_lane = 4 * lane >= HALO && 4 * lane < HALO + WOUT;
 
-  // Input row y of an item whose first row has ring slot `bslot` lives in
-  // slot (bslot + y) % Rin; consecutive items continue the ring, so the next
-  // item's first batch is fetched during the current item's last one.
-  // One warp copies one (plane, row) at a time, a lane per 16-byte chunk.
-  auto prefetch = [&](int item, int q, int bslot) {
-    if (item < n_items) {
-      const int li = item / per_img, rem = item - li * per_img;
-      const int y0 = (rem / strips) * H, x0 = (rem % strips) * GF_W;
-      const ImgDesc& d = imgs[cd.img0 + li];
-      const float* planes[2] = {d.uI, d.up};
-      const int r0 = q * GF_RB;
-      const int rows = min(GF_RB, nrows - r0);
-      const int lane = tid & 31;
-      if (lane < G::CW) {
-        const int gx = (x0 - 4 * G::Q + 4 * lane) & (N - 1);
-        for (int pr = tid >> 5; pr < 2 * rows; pr += GF_THREADS / 32) {
-          const int plane = pr & 1, row = pr >> 1;
-          const int gy = (y0 - 2 * RAD + r0 + row) & (M - 1);
-          const int slot = (bslot + r0 + row) % Rin;
-          cp_async16((plane ? inP : inI) + slot * IP + 4 * lane, planes[plane] + (size_t)gy * N + gx);
-        }
-      }
-    }
-    cp_async_commit();
-  };
-
-  int item = blockIdx.x;
-  int bslot = 0;
-  prefetch(item, 0, bslot);
-  while (item < n_items) {
+  for (int item = gwarp; item < n_items; item += nwarps) {
     const int li = item / per_img, rem = item - li * per_img;
-    const int y0 = (rem / strips) * H, x0 = (rem % strips) * GF_W;
+    const int y0 = (rem / strips) * H, x0 = (rem % strips) * WOUT;
     const int gi = cd.img0 + li;
     const ImgDesc& d = imgs[gi];
-    float* const u_out = d.u;
+    const float* __restrict__ I = d.uI;
+    const float* __restrict__ P = d.up;
     const float* uo = (iter >= 0 && d.isnr_out) ? d.uo : nullptr;
+    // this lane's 4 columns (16-byte aligned: x0 and HALO are multiples of 4)
+    const int gx = (x0 - HALO + 4 * lane) & (N - 1);
+    const bool store = out_lane && x0 + 4 * lane - HALO < N;
     float cI = 0.0f, cP = 0.0f;
     if (shifted) {
-      const size_t c = (size_t)((y0 + H / 2) & (M - 1)) * N + ((x0 + GF_W / 2) & (N - 1));
-      cI = __ldg(&d.uI[c]);
-      cP = __ldg(&d.up[c]);
+      const size_t c = (size_t)((y0 + H / 2) & (M - 1)) * N + ((x0 + WOUT / 2) & (N - 1));
+      cI = __ldg(&I[c]);
+      cP = __ldg(&P[c]);
     }
     const float eps = (float)d.eps;
+    // input row j of the item is image row y0 - 2r + j, ring slot j % RI
+    const int nin = H + 4 * RAD;
+    auto fetch = [&](int j) {
+      if (j < nin) {
+        const size_t off = (size_t)((y0 - 2 * RAD + j) & (M - 1)) * N + gx;
+        cp_async16(rI + (j % RI) * GFW_COLS + 4 * lane, I + off);
+        cp_async16(rP + (j % RI) * GFW_COLS + 4 * lane, P + off);
+      }
+    };
+    auto ring4 = [&](const float* r, int j) {
+      return reinterpret_cast<const float4*>(r + (j % RI) * GFW_COLS)[lane];
+    };
+    for (int j = 0; j <= 2 * RAD; ++j) fetch(j);
+    cp_async_commit();
+    float V[4][4];   // [J, Q, J^2, J Q][column]: window sums down the columns
+    float VA[2][4];  // [a, b][column]
     float err = 0.0f;
-    const int next_bslot = (bslot + nq * GF_RB) % Rin;
-    for (int q = 0; q < nq; ++q) {
-      cp_async_wait<0>();
-      __syncthreads();
-      if (q + 1 < nq)
-        prefetch(item, q + 1, bslot);
-      else
-        prefetch(item + gridDim.x, 0, next_bslot);
-      const int r0 = q * GF_RB;
-      const int rows = min(GF_RB, nrows - r0);
-      const int s_r0 = (bslot + r0) % Rin;  // ring slot of input row r0
-      // 1. column window sums of J, Q, J^2, J Q for rows y >= 2r of the batch
-      //    (window rows y-2r .. y)
-      for (int u = tid; u < WU * NSB; u += GF_THREADS) {
-        const int c = u % WU, sb = u / WU;
-        const int lo = max(sb * GF_SB, 2 * RAD - r0);
-        const int hi = min(sb * GF_SB + GF_SB, rows);
-        if (lo >= hi) continue;
-        const float* cI_col = inI + c + OFF;
-        const float* cP_col = inP + c + OFF;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int sl = s_r0 + lo;
-        if (sl >= Rin) sl -= Rin;
-        {
-          int t = sl;
+    // stats row s (image row y0 - r + s) has its column window on input rows
+    // j = s .. s + 2r; output row t = s - 2r needs stats rows t .. t + 2r
+    for (int s = 0; s < H + 2 * RAD; ++s) {
+      fetch(s + 2 * RAD + 1);  // its slot held row s - 2, no longer needed
+      cp_async_commit();
+      cp_async_wait<1>();      // rows up to s + 2r have landed
+      if (s % GFW_SUB == 0) {
 #pragma unroll
-          for (int dd = 0; dd < WIN; ++dd) {
-            const float J = cI_col[t * IP] - cI, Qv = cP_col[t * IP] - cP;
-            s0 += J;
-            s1 += Qv;
-            s2 = fmaf(J, J, s2);
-            s3 = fmaf(J, Qv, s3);
-            t = wrap_dec(t, Rin);
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) V[q][k] = 0.0f;
+#pragma unroll
+        for (int dd = 0; dd < WIN; ++dd) {
+          const float4 iv = ring4(rI, s + dd), pv = ring4(rP, s + dd);
+          const float J[4] = {iv.x - cI, iv.y - cI, iv.z - cI, iv.w - cI};
+          const float Q[4] = {pv.x - cP, pv.y - cP, pv.z - cP, pv.w - cP};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            V[0][k] += J[k];
+            V[1][k] += Q[k];
+            V[2][k] = fmaf(J[k], J[k], V[2][k]);
+            V[3][k] = fmaf(J[k], Q[k], V[3][k]);
           }
         }
-        float* v = vs + lo * VP + c;
-        v[0] = s0;
-        v[PS] = s1;
-        v[2 * PS] = s2;
-        v[3 * PS] = s3;
-        for (int rho = lo + 1; rho < hi; ++rho) {
-          sl = wrap_inc(sl, Rin);
-          const int so = wrap_sub(sl, WIN, Rin);
-          const float Jn = cI_col[sl * IP] - cI, Qn = cP_col[sl * IP] - cP;
-          const float Jo = cI_col[so * IP] - cI, Qo = cP_col[so * IP] - cP;
-          s0 += Jn - Jo;
-          s1 += Qn - Qo;
-          s2 += fmaf(Jn, Jn, -Jo * Jo);
-          s3 += fmaf(Jn, Qn, -Jo * Qo);
-          v += VP;
-          v[0] = s0;
-          v[PS] = s1;
-          v[2 * PS] = s2;
-          v[3 * PS] = s3;
+      } else {
+        const float4 in = ring4(rI, s + 2 * RAD), pn = ring4(rP, s + 2 * RAD);
+        const float4 io = ring4(rI, s - 1), po = ring4(rP, s - 1);
+        const float Jn[4] = {in.x - cI, in.y - cI, in.z - cI, in.w - cI};
+        const float Qn[4] = {pn.x - cP, pn.y - cP, pn.z - cP, pn.w - cP};
+        const float Jo[4] = {io.x - cI, io.y - cI, io.z - cI, io.w - cI};
+        const float Qo[4] = {po.x - cP, po.y - cP, po.z - cP, po.w - cP};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          V[0][k] += Jn[k] - Jo[k];
+          V[1][k] += Qn[k] - Qo[k];
+          V[2][k] += fmaf(Jn[k], Jn[k], -Jo[k] * Jo[k]);
+          V[3][k] += fmaf(Jn[k], Qn[k], -Jo[k] * Qo[k]);
         }
       }
-      __syncthreads();
-      // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4); the (a, b) row of
-      //    input row y goes to ring slot y % Rab
-      {
-        constexpr int RUNS = (W1 + GF_C - 1) / GF_C;
-        for (int u = tid; u < GF_RB * RUNS; u += GF_THREADS) {
-          const int rho = u % GF_RB, run = u / GF_RB;
-          const int y = r0 + rho;
-          if (rho >= rows || y < 2 * RAD) continue;
-          const float* v = vs + rho * VP + run * GF_C;
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4)
+      float S0[4], S1[4], S2[4], S3[4];
+      hsum4<RAD>(V[0], S0);
+      hsum4<RAD>(V[1], S1);
+      hsum4<RAD>(V[2], S2);
+      hsum4<RAD>(V[3], S3);
+      float A[4], B[4];
 #pragma unroll
-          for (int dd = 0; dd < WIN; ++dd) {
-            s0 += v[dd];
-            s1 += v[PS + dd];
-            s2 += v[2 * PS + dd];
-            s3 += v[3 * PS + dd];
-          }
-          const int slot = y % Rab;
-          float* ar = abA + slot * AP + run * GF_C;
-          float* br = abB + slot * AP + run * GF_C;
+      for (int k = 0; k < 4; ++k) {
+        const float mJ = S0[k] * inv_n, mQ = S1[k] * inv_n;
+        const float var = fmaf(-mJ, mJ, S2[k] * inv_n);  // sigma_k^2
+        const float cov = fmaf(-mJ, mQ, S3[k] * inv_n);  // mean(I p) - mu pbar
+        A[k] = __fdividef(cov, var + eps);  // var + eps >= eps > 0
+        B[k] = (mQ + cP) - A[k] * (mJ + cI);
+      }
+      // 3. ring slot s % WIN holds stats row s - WIN until overwritten here
+      float4* const sa = reinterpret_cast<float4*>(ra + (s % WIN) * GFW_COLS) + lane;
+      float4* const sb = reinterpret_cast<float4*>(rb + (s % WIN) * GFW_COLS) + lane;
+      const int t = s - 2 * RAD;  // output row (if >= 0)
+      const bool slide = t > 0 && t % GFW_SUB != 0;
+      if (slide) {
+        const float4 oa = *sa, ob = *sb;
+        VA[0][0] += A[0] - oa.x;
+        VA[0][1] += A[1] - oa.y;
+        VA[0][2] += A[2] - oa.z;
+        VA[0][3] += A[3] - oa.w;
+        VA[1][0] += B[0] - ob.x;
+        VA[1][1] += B[1] - ob.y;
+        VA[1][2] += B[2] - ob.z;
+        VA[1][3] += B[3] - ob.w;
+      }
+      *sa = make_float4(A[0], A[1], A[2], A[3]);
+      *sb = make_float4(B[0], B[1], B[2], B[3]);
+      if (t < 0) continue;
+      if (!slide) {  // direct: the ring holds stats rows t .. t + 2r
 #pragma unroll
-          for (int c = 0; c < GF_C; ++c) {
-            if (run * GF_C + c >= W1) break;
-            if (c > 0) {
-              s0 += v[c + 2 * RAD] - v[c - 1];
-              s1 += v[PS + c + 2 * RAD] - v[PS + c - 1];
-              s2 += v[2 * PS + c + 2 * RAD] - v[2 * PS + c - 1];
-              s3 += v[3 * PS + c + 2 * RAD] - v[3 * PS + c - 1];
-            }
-            const float mJ = s0 * inv_n, mQ = s1 * inv_n;
-            const float var = fmaf(-mJ, mJ, s2 * inv_n);  // sigma_k^2
-            const float cov = fmaf(-mJ, mQ, s3 * inv_n);  // mean(I p) - mu pbar
-            const float a = cov / (var + eps);
-            ar[c] = a;
-            br[c] = (mQ + cP) - a * (mJ + cI);
-          }
+        for (int k = 0; k < 4; ++k) VA[0][k] = VA[1][k] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < WIN; ++q) {
+          const float4 a4 = reinterpret_cast<const float4*>(ra + q * GFW_COLS)[lane];
+          const float4 b4 = reinterpret_cast<const float4*>(rb + q * GFW_COLS)[lane];
+          VA[0][0] += a4.x;
+          VA[0][1] += a4.y;
+          VA[0][2] += a4.z;
+          VA[0][3] += a4.w;
+          VA[1][0] += b4.x;
+          VA[1][1] += b4.y;
+          VA[1][2] += b4.z;
+          VA[1][3] += b4.w;
         }
       }
-      __syncthreads();
-      // 3. column window sums of a and b for rows y >= 4r (a, b rows y-2r .. y)
-      for (int u = tid; u < W1 * NSB; u += GF_THREADS) {
-        const int c = u % W1, sb = u / W1;
-        const int lo = max(sb * GF_SB, 4 * RAD - r0);
-        const int hi = min(sb * GF_SB + GF_SB, rows);
-        if (lo >= hi) continue;
-        const float* a_col = abA + c;
-        const float* b_col = abB + c;
-        int sl = (r0 + lo) % Rab;
-        float sa = 0.f, sb_ = 0.f;
-        {
-          int t = sl;
+      // 4. row window sums of a, b -> u = abar I + bbar (Eq. 5); the guidance
+      //    at output row t is input row j = t + 2r = s
+      float SA[4], SB[4];
+      hsum4<RAD>(VA[0], SA);
+      hsum4<RAD>(VA[1], SB);
+      const float4 iv = ring4(rI, s);
+      const float ic[4] = {iv.x, iv.y, iv.z, iv.w};
+      float o[4];
 #pragma unroll
-          for (int dd = 0; dd < WIN; ++dd) {
-            sa += a_col[t * AP];
-            sb_ += b_col[t * AP];
-            t = wrap_dec(t, Rab);
-          }
-        }
-        vsA[lo * AP + c] = sa;
-        vsB[lo * AP + c] = sb_;
-        for (int rho = lo + 1; rho < hi; ++rho) {
-          sl = wrap_inc(sl, Rab);
-          const int so = wrap_sub(sl, WIN, Rab);
-          sa += a_col[sl * AP] - a_col[so * AP];
-          sb_ += b_col[sl * AP] - b_col[so * AP];
-          vsA[rho * AP + c] = sa;
-          vsB[rho * AP + c] = sb_;
-        }
-      }
-      __syncthreads();
-      // 4. row window sums -> u = abar I + bbar (Eq. 5) for output row y - 4r,
-      //    GF_C consecutive outputs per thread, one 16-byte store
-      {
-        static_assert(GF_W / GF_C * GF_RB == GF_THREADS, "one unit per thread");
-        const int rho = tid % GF_RB, run = tid / GF_RB;
-        const int y = r0 + rho;
-        const int x = run * GF_C;
-        if (rho < rows && y >= 4 * RAD && (N >= GF_W || x < N)) {
-          const float* va = vsA + rho * AP + x;
-          const float* vb = vsB + rho * AP + x;
-          int si = s_r0 + rho - 2 * RAD;  // input row y - 2r
-          if (si < 0) si += Rin;
-          if (si >= Rin) si -= Rin;
-          const float* ri = inI + si * IP + x + 2 * RAD + OFF;
-          float sa = 0.f, sb_ = 0.f;
-#pragma unroll
-          for (int dd = 0; dd < WIN; ++dd) {
-            sa += va[dd];
-            sb_ += vb[dd];
-          }
-          float o[GF_C];
-#pragma unroll
-          for (int c = 0; c < GF_C; ++c) {
-            if (c > 0) {
-              sa += va[c + 2 * RAD] - va[c - 1];
-              sb_ += vb[c + 2 * RAD] - vb[c - 1];
-            }
-            o[c] = fmaf(sa * inv_n, ri[c], sb_ * inv_n);
-          }
-          const int gy = (y0 + y - 4 * RAD) & (M - 1);
-          const size_t off = (size_t)gy * N + x0 + x;
-          *reinterpret_cast<float4*>(u_out + off) = make_float4(o[0], o[1], o[2], o[3]);
-          if (uo) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(uo + off));
-            const float e0 = o[0] - t.x, e1 = o[1] - t.y, e2 = o[2] - t.z, e3 = o[3] - t.w;
-            err = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, err))));
-          }
+      for (int k = 0; k < 4; ++k) o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n);
+      if (store) {
+        const size_t off = (size_t)((y0 + t) & (M - 1)) * N + gx;
+        *reinterpret_cast<float4*>(d.u + off) = make_float4(o[0], o[1], o[2], o[3]);
+        if (uo) {
+          const float4 g = __ldg(reinterpret_cast<const float4*>(uo + off));
+          const float e0 = o[0] - g.x, e1 = o[1] - g.y, e2 = o[2] - g.z, e3 = o[3] - g.w;
+          err = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, err))));
         }
       }
     }
+    cp_async_wait<0>();  // the ring is reused by the next item
     if (uo) {
-      // ||u - u_orig||^2 of this item (FP32 in a warp, FP64 across warps)
+      // ||u - u_orig||^2 of this item: FP32 in the warp, FP64 across items
       err = warp_sum(err);
-      if ((tid & 31) == 0) red[tid >> 5] = (double)err;
-      __syncthreads();
-      ImgState* S = st + gi;
-      if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < GF_THREADS / 32; ++w) s += red[w];
-        atomicAdd(&S->err2, s);
+      if (lane == 0) {
+        ImgState* S = st + gi;
+        atomicAdd(&S->err2, (double)err);
         __threadfence();
         const unsigned int prev = atomicAdd(&S->gf_done, 1u);
-        *s_flag = (prev == (unsigned)per_img - 1);
-      }
-      __syncthreads();
-      if (*s_flag && tid == 0) {
-        __threadfence();
-        const double e2 = __ldcg(&S->err2);
-        d.isnr_out[iter] = 10.0 * log10(S->den_isnr / e2);
-        S->err2 = 0.0;
-        S->gf_done = 0;
-        __threadfence();
+        if (prev == (unsigned)per_img - 1) {
+          __threadfence();
+          const double e2 = __ldcg(&S->err2);
+          d.isnr_out[iter] = 10.0 * log10(S->den_isnr / e2);
+          S->err2 = 0.0;
+          S->gf_done = 0;
+          __threadfence();
+        }
       }
     }
-    bslot = next_bslot;
-    item += gridDim.x;
+    __syncwarp();
   }
-  cp_async_wait<0>();
 }
 
-__global__ void __launch_bounds__(GF_THREADS, 3)
+__global__ void __launch_bounds__(GFW_WARPS * 32)
 k_guided_filter(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
                 int plain_var, int rad, int H) {
   extern __shared__ __align__(16) float gsm[];
-  __shared__ double red[GF_THREADS / 32];
-  __shared__ int s_flag;
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = blockIdx.x * GFW_WARPS + warp;
+  const int nwarps = gridDim.x * GFW_WARPS;
+  float* ring = gsm + (size_t)warp * gfw_ring_floats(rad);
   const bool shifted = plain_var == 0;
   switch (rad) {
-    case 0: gf_items<0>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 1: gf_items<1>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 2: gf_items<2>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 3: gf_items<3>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 4: gf_items<4>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 5: gf_items<5>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 6: gf_items<6>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    case 7: gf_items<7>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
-    default: gf_items<8>(cd, imgs, st, iter, shifted, H, gsm, red, &s_flag); break;
+    case 0: gfw_items<0>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 1: gfw_items<1>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 2: gfw_items<2>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 3: gfw_items<3>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 4: gfw_items<4>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 5: gfw_items<5>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 6: gfw_items<6>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    case 7: gfw_items<7>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    default: gfw_items<8>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
   }
 }
 
@@ -373,31 +296,37 @@ static int gf_sm_count() {
 }
 
 // One launch per window radius present in the class (the images of a class
-// are ordered by radius, so each group is a contiguous range).
+// are ordered by radius, so each group is a contiguous range).  Items are
+// (image, strip, block of H rows); H is halved (down to 16) while there are
+// fewer items than resident warps.
 cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, cudaStream_t s) {
-  const int H = c.cd.M < GF_H ? c.cd.M : GF_H;
-  const int strips = c.cd.N >= GF_W ? c.cd.N / GF_W : 1;
   for (int g = 0; g < c.n_rad_groups; ++g) {
     const RadGroup& rg = c.rad_groups[g];
     ClassDesc cd = c.cd;
     cd.img0 = rg.img0;
     cd.n_img = rg.n_img;
-    const size_t smem = gf_smem_bytes(rg.rad);
+    const size_t smem = (size_t)GFW_WARPS * gfw_ring_floats(rg.rad) * sizeof(float);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_guided_filter, GF_THREADS, smem) !=
-            cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_guided_filter, GFW_WARPS * 32,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
       per_sm = 1;
+    const int warps = per_sm * gf_sm_count() * GFW_WARPS;
+    const int strips = (cd.N + gfw_wout(rg.rad) - 1) / gfw_wout(rg.rad);
+    int H = cd.M < 64 ? cd.M : 64;
+    while (H > 16 && cd.n_img * strips * (cd.M / H) < warps) H /= 2;
     const int n_items = cd.n_img * strips * (cd.M / H);
     int grid = per_sm * gf_sm_count();
-    if (grid > n_items) grid = n_items;
-    k_guided_filter<<<grid, GF_THREADS, smem, s>>>(cd, c.imgs, c.st, iter, plain_var, rg.rad, H);
+    const int need = (n_items + GFW_WARPS - 1) / GFW_WARPS;
+    if (grid > need) grid = need;
+    k_guided_filter<<<grid, GFW_WARPS * 32, smem, s>>>(cd, c.imgs, c.st, iter, plain_var, rg.rad, H);
   }
   return cudaGetLastError();
 }
 
 cudaError_t configure_gf_kernel() {
   return cudaFuncSetAttribute(k_guided_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)gf_smem_bytes(GF_RMAX));
+                              (int)(GFW_WARPS * gfw_ring_floats(GF_RMAX) * sizeof(float)));
 }
 
 }  // namespace gfd
