@@ -3,7 +3,7 @@
 //
 // Every warp works alone, down a strip of GFW_COLS input columns (4 per
 // lane): no block barriers.  Input rows enter a per-warp ring in shared
-// memory by 16-byte asynchronous copies two rows ahead of use; each lane
+// memory by 16-byte asynchronous copies GFW_AHEAD rows ahead of use; each lane
 // copies and reads only its own 4 columns.  For the item's rows the warp
 // forms, row by row,
 //   1. window sums down its columns of J = I - c_I, Q = p - c_p, J^2, J Q
@@ -31,19 +31,22 @@ namespace gfd {
 constexpr int GFW_COLS = 128;   // input columns per strip (4 per lane)
 constexpr int GFW_SUB = 8;      // rows between direct re-formations of the column sums
 constexpr int GFW_WARPS = 4;    // warps per block
+constexpr int GFW_AHEAD = 2;    // input rows requested ahead of use
 constexpr int GF_RMAX = 8;      // w <= 17
 constexpr unsigned FULL = 0xffffffffu;
 
 template <int RAD>
 struct GfwGeom {
   static constexpr int WIN = 2 * RAD + 1;
-  static constexpr int RI = WIN + 3;  // input ring rows: window, the row leaving, two ahead
+  static constexpr int RI = WIN + 1 + GFW_AHEAD;  // input ring rows: window, the row leaving, ahead
   static constexpr int HALO = 4 * ((RAD + 1) / 2);  // >= 2r, multiple of 4
   static constexpr int WOUT = GFW_COLS - 2 * HALO;  // output columns per strip
 };
 
-// per-warp shared memory: (a, b) ring of 2r+1 rows, (I, p) ring of 2r+4 rows
-GFD_HD int gfw_ring_floats(int rad) { return (2 * (2 * rad + 1) + 2 * (2 * rad + 4)) * GFW_COLS; }
+// per-warp shared memory: (a, b) ring of 2r+1 rows, (I, p) ring of 2r+2+GFW_AHEAD rows
+GFD_HD int gfw_ring_floats(int rad) {
+  return (2 * (2 * rad + 1) + 2 * (2 * rad + 2 + GFW_AHEAD)) * GFW_COLS;
+}
 static int gfw_wout(int rad) { return GFW_COLS - 8 * ((rad + 1) / 2); }
 
 // Window sums of radius RAD along the strip: v[k] is column 4*lane + k;
@@ -127,17 +130,20 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
     };
     for (int j = 0; j <= 2 * RAD; ++j) fetch(j);
     cp_async_commit();
-    fetch(2 * RAD + 1);
-    cp_async_commit();
+#pragma unroll
+    for (int a = 1; a < GFW_AHEAD; ++a) {
+      fetch(2 * RAD + a);
+      cp_async_commit();
+    }
     float V[4][4];   // [J, Q, J^2, J Q][column]: window sums down the columns
     float VA[2][4];  // [a, b][column]
     float err = 0.0f;
     // stats row s (image row y0 - r + s) has its column window on input rows
     // j = s .. s + 2r; output row t = s - 2r needs stats rows t .. t + 2r
     for (int s = 0; s < H + 2 * RAD; ++s) {
-      fetch(s + 2 * RAD + 2);  // two rows ahead; its slot held row s - 2, no longer needed
+      fetch(s + 2 * RAD + GFW_AHEAD);  // its slot held row s - 2, no longer needed
       cp_async_commit();
-      cp_async_wait<2>();      // rows up to s + 2r have landed
+      cp_async_wait<GFW_AHEAD>();      // rows up to s + 2r have landed
       const int t = s - 2 * RAD;  // output row (if >= 0)
       // the reference row of the ISNR sums is requested early (used last)
       float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
