@@ -138,8 +138,9 @@ struct DFT<2, INV> {
 };
 
 // tw: the table of the transform length L (W_L^m, m < L)
+// (a generic load: the table may sit in shared or global memory)
 GFD_D float2 twiddle(const float2* __restrict__ tw, int m, bool inv) {
-  float2 w = __ldg(&tw[m]);
+  float2 w = tw[m];
   if (inv) w.y = -w.y;
   return w;
 }

@@ -35,6 +35,9 @@ GFD_D float2* cplx_plane(const ImgDesc& d, int sel) {
 }
 
 constexpr int threads_per_team(int L) { return L / radix_for(L); }
+// Largest column length whose twiddle table the column passes keep in
+// shared memory (8 KB at 1024).
+constexpr int SMEM_TW_MAX = 1024;
 
 // Persistent pass kernels.  Each block walks the work items item =
 // blockIdx.x + k * gridDim.x; the inputs of the next item are copied
@@ -308,6 +311,14 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   float2* landS = smem;
   float2* work = landS + tile;
   double* red = reinterpret_cast<double*>(work + B * ts);
+  // the length-M twiddle table, copied once per (persistent) block for
+  // M <= SMEM_TW_MAX; larger tables stay in global memory
+  const float2* twM = tw + tab_off(M);
+  if constexpr (M <= SMEM_TW_MAX) {
+    float2* stw = reinterpret_cast<float2*>(red + num_warps() * (KNODES + 1));
+    for (int i = threadIdx.x; i < M; i += blockDim.x) stw[i] = twM[i];
+    twM = stw;  // visible after the loop's first __syncthreads()
+  }
   // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
   const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
@@ -373,10 +384,10 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
       if (threadIdx.x == 0) S->sum_u = s_tot[0];
     }
     float2* buf = work + b * ts;
-    Stage0From<M, R, false>::run(landS + b, StridedIdx{B}, buf, j, tw + tab_off(M), PaddedIdx());
+    Stage0From<M, R, false>::run(landS + b, StridedIdx{B}, buf, j, twM, PaddedIdx());
     __syncthreads();  // the landing tile is consumed
     issue(item + 1);
-    Stage<M, R, false, 1>::run(work + bf * ts, jf, tw + tab_off(M), PaddedIdx());  // ends synchronised
+    Stage<M, R, false, 1>::run(work + bf * ts, jf, twM, PaddedIdx());  // ends synchronised
     float nodes[KNODES];
 #pragma unroll
     for (int q = 0; q < KNODES; ++q) nodes[q] = s_nodes[q];
@@ -549,6 +560,12 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
   float2* landU = smem;
   float2* workI = landU + tile;
   float2* workP = workI + B * ts;
+  const float2* twM = tw + tab_off(M);
+  if constexpr (M <= SMEM_TW_MAX) {
+    float2* stw = workP + B * ts;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) stw[i] = twM[i];
+    twM = stw;  // visible after the loop's first __syncthreads()
+  }
   // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
   const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
@@ -602,7 +619,7 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     }
     __syncthreads();
     issue(item + gridDim.x);
-    fft_team2<M, true>(workI + bf * ts, workP + bf * ts, jf, tw + tab_off(M));
+    fft_team2<M, true>(workI + bf * ts, workP + bf * ts, jf, twM);
     float2* qi = d.QI + off + b;
     float2* qp = d.Qp + off + b;
 #pragma unroll 4
@@ -777,7 +794,8 @@ template <int M>
 static size_t col_smem(int B, int landings, int works, int nthr) {
   return (size_t)landings * M * B * sizeof(float2) +
          (size_t)works * B * col_team_stride(M, B) * sizeof(float2) +
-         (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double);
+         (size_t)((nthr + 31) / 32) * (KNODES + 1) * sizeof(double) +
+         (M <= SMEM_TW_MAX ? (size_t)M * sizeof(float2) : 0);
 }
 
 template <int M>
