@@ -65,6 +65,13 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
   float2* work = land + item_elems;
   float2* outb = work + rpc * team_stride(L);
   double* red = reinterpret_cast<double*>(outb + item_elems);
+  // length-L twiddle table in shared memory (L <= SMEM_TW_MAX)
+  const float2* twL = tw + tab_off(L);
+  if constexpr (L <= SMEM_TW_MAX) {
+    float2* stw = reinterpret_cast<float2*>(red + 32);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) stw[i] = twL[i];
+    twL = stw;  // visible after the loop's first __syncthreads()
+  }
   const int team = threadIdx.x / T, j = threadIdx.x % T;
   const int n_items = cd.n_img * M / rpc;
   auto issue = [&](int item) {
@@ -96,7 +103,7 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
       part = warp_sum(part);
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)part;
     }
-    fft_team_from<L, false>(in, IdentIdx(), buf, j, tw + tab_off(L));  // first stage reads land
+    fft_team_from<L, false>(in, IdentIdx(), buf, j, twL);  // first stage reads land
     issue(item + gridDim.x);                               // land is free again
     if (do_sum && threadIdx.x == 0) {
       double s = 0.0;
@@ -152,6 +159,12 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
   const int item_elems = rpc * L;
   float2* land = smem;
   float2* work = smem + item_elems;
+  const float2* twL = tw + tab_off(L);
+  if constexpr (L <= SMEM_TW_MAX) {
+    float2* stw = work + rpc * team_stride(L);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) stw[i] = twL[i];
+    twL = stw;  // visible after the loop's first __syncthreads()
+  }
   const int team = threadIdx.x / T, j = threadIdx.x % T;
   const int per_plane = cd.n_img * M / rpc;
   const int n_items = sel1 >= 0 ? 2 * per_plane : per_plane;
@@ -209,7 +222,7 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
     }
     __syncthreads();
     issue(item + gridDim.x);
-    fft_team<L, true>(buf, j, tw + tab_off(L));
+    fft_team<L, true>(buf, j, twL);
     float2* rowp = reinterpret_cast<float2*>(real_plane(d, dsel)) + (size_t)row * L;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -692,10 +705,11 @@ int class_tile_width(int M, int N) {
 
 static size_t row_r2c_smem(int L, int rpc) {
   return (size_t)2 * rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
-         32 * sizeof(double);
+         32 * sizeof(double) + (L <= SMEM_TW_MAX ? (size_t)L * sizeof(float2) : 0);
 }
 static size_t row_c2r_smem(int L, int rpc) {
-  return (size_t)rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2);
+  return (size_t)rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
+         (L <= SMEM_TW_MAX ? (size_t)L * sizeof(float2) : 0);
 }
 
 #define GFD_CASE_L(F, ...)             \
