@@ -484,38 +484,52 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
   for (int q = 0; q <= KNODES; ++q) acc[q] = 0.0f;
   const int e0 = (blockIdx.x % cpi) * chunk;
   const int lg_tile = __ffs(M * TB) - 1, lg_tb = __ffs(TB) - 1;  // powers of two
-  // runs of 16 bins per thread between folds (uniform control flow)
-  for (int base = e0; base < e0 + chunk; base += 16 * blockDim.x) {
-   for (int q = 0; q < 16; ++q) {
-    const int e = base + q * blockDim.x + threadIdx.x;
-    if (e >= e0 + chunk) break;
-    const int t = e >> lg_tile, rem = e & ((1 << lg_tile) - 1);
-    const int k = rem >> lg_tb, b = rem & (TB - 1);
-    const int col = t * TB + b;
-    const float2 U = d.S[e];
-    if (col != 0) {
-      const float2 H = __ldg(&d.H[e]), Y = __ldg(&d.Y[e]);
-      const float2 r = csub(cmul(H, U), Y);
-      accum_bin(2.0f * fmaf(r.x, r.x, r.y * r.y), fmaf(H.x, H.x, H.y * H.y), nodes, acc);
-    } else {
-      const float2 Um = d.S[(size_t)((M - k) & (M - 1)) * TB];
-      float2 UA, UB;
-      unpack_pair(U, Um, UA, UB);
-      const float2 HA = d.H0[k], HB = d.HN[k], YA = d.Y0[k], YB = d.YN[k];
-      float rA;
-      if (k == 0) {
-        const double d00 = __ldcg(&S->d00);
-        rA = (float)(d00 * d00);
-      } else {
-        const float2 r = csub(cmul(HA, UA), YA);
-        rA = fmaf(r.x, r.x, r.y * r.y);
+  // bins in pairs (b, b+1) of one tile row, read as 16-byte vectors; runs of
+  // 8 pairs per thread between folds (uniform control flow)
+  const float4* S4 = reinterpret_cast<const float4*>(d.S);
+  const float4* H4 = reinterpret_cast<const float4*>(d.H);
+  const float4* Y4 = reinterpret_cast<const float4*>(d.Y);
+  const int pairs = chunk / 2, p0 = e0 / 2;
+  for (int base = 0; base < pairs; base += 8 * blockDim.x) {
+#pragma unroll 4
+    for (int q = 0; q < 8; ++q) {
+      const int pi = base + q * blockDim.x + threadIdx.x;
+      if (pi < pairs) {
+        const int e = 2 * (p0 + pi);
+        const int t = e >> lg_tile, rem = e & ((1 << lg_tile) - 1);
+        const int k = rem >> lg_tb, b = rem & (TB - 1);  // b even
+        const float4 U2 = __ldcs(&S4[p0 + pi]);
+        const float4 H2 = __ldg(&H4[p0 + pi]), Y2 = __ldg(&Y4[p0 + pi]);
+        {  // bin b + 1 (never column 0)
+          const float2 H = make_float2(H2.z, H2.w);
+          const float2 r = csub(cmul(H, make_float2(U2.z, U2.w)), make_float2(Y2.z, Y2.w));
+          accum_bin(2.0f * fmaf(r.x, r.x, r.y * r.y), fmaf(H.x, H.x, H.y * H.y), nodes, acc);
+        }
+        if (t != 0 || b != 0) {
+          const float2 H = make_float2(H2.x, H2.y);
+          const float2 r = csub(cmul(H, make_float2(U2.x, U2.y)), make_float2(Y2.x, Y2.y));
+          accum_bin(2.0f * fmaf(r.x, r.x, r.y * r.y), fmaf(H.x, H.x, H.y * H.y), nodes, acc);
+        } else {  // packed column 0: bins (k, 0) and (k, N/2)
+          const float2 U = make_float2(U2.x, U2.y);
+          const float2 Um = d.S[(size_t)((M - k) & (M - 1)) * TB];
+          float2 UA, UB;
+          unpack_pair(U, Um, UA, UB);
+          const float2 HA = d.H0[k], HB = d.HN[k], YA = d.Y0[k], YB = d.YN[k];
+          float rA;
+          if (k == 0) {
+            const double d00 = __ldcg(&S->d00);
+            rA = (float)(d00 * d00);
+          } else {
+            const float2 r = csub(cmul(HA, UA), YA);
+            rA = fmaf(r.x, r.x, r.y * r.y);
+          }
+          const float2 rb = csub(cmul(HB, UB), YB);
+          accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
+          accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
+        }
       }
-      const float2 rb = csub(cmul(HB, UB), YB);
-      accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
-      accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
     }
-   }
-   warp_fold(acc, &s_wacc);
+    warp_fold(acc, &s_wacc);
   }
   block_partials_folded(&s_wacc, d.part + (size_t)(blockIdx.x % cpi) * (KNODES + 1));
   if (last_item(&S->cta_done, cpi, &s_flag)) {
