@@ -10,17 +10,26 @@
 
 #include "launch.h"
 
+#ifndef GFD_CHAINS
+#define GFD_CHAINS 4
+#endif
+
 using namespace gfd;
 
 namespace {
 
 constexpr int AUX_SLOTS = 8;
+constexpr int CHAINS = GFD_CHAINS;
 
 struct Plan {
   std::vector<unsigned char> key;
   int n = 0, iters = 0;
   std::vector<int> order;                // internal index -> user index
   std::vector<ClassLaunch> classes;
+  // the iterations of the graph-captured solve run as CHAINS concurrent
+  // chains over parts of every class, so that the blocks of different phases
+  // share the SMs (a kernel's tail overlaps the next kernel of another chain)
+  std::vector<ClassLaunch> parts[CHAINS];
   std::vector<ImgDesc> h_imgs;           // internal order
   std::vector<gfdeconv_image> user;      // internal order
   cudaGraphExec_t exec = nullptr;
@@ -72,6 +81,9 @@ struct gfdeconv_ctx {
   float* d2 = nullptr;
   float4* twdf = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t side[CHAINS - 1] = {};  // further chains of a captured solve
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[CHAINS - 1] = {};
   char* ws = nullptr;
   size_t ws_bytes = 0;
   ImgDesc* d_imgs = nullptr;
@@ -278,6 +290,29 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
     }
     pl.classes.push_back(cl);
   }
+  // parts: CHAINS consecutive runs of the images of every class, with their
+  // window-radius groups cut to the range
+  for (auto& v : pl.parts) v.clear();
+  for (const ClassLaunch& cl : pl.classes) {
+    for (int part = 0; part < CHAINS; ++part) {
+      const int lo = cl.cd.img0 + (int)((long long)cl.cd.n_img * part / CHAINS);
+      const int hi = cl.cd.img0 + (int)((long long)cl.cd.n_img * (part + 1) / CHAINS);
+      if (hi <= lo) continue;
+      ClassLaunch q = cl;
+      q.cd.img0 = lo;
+      q.cd.n_img = hi - lo;
+      q.n_rad_groups = 0;
+      q.max_rad = 0;
+      for (int g = 0; g < cl.n_rad_groups; ++g) {
+        const RadGroup& rg = cl.rad_groups[g];
+        const int a0 = std::max(rg.img0, lo), a1 = std::min(rg.img0 + rg.n_img, hi);
+        if (a1 <= a0) continue;
+        q.rad_groups[q.n_rad_groups++] = RadGroup{a0, a1 - a0, rg.rad};
+        q.max_rad = std::max(q.max_rad, rg.rad);
+      }
+      pl.parts[part].push_back(q);
+    }
+  }
   return cudaMemcpy(c->d_imgs, pl.h_imgs.data(), sizeof(ImgDesc) * n, cudaMemcpyHostToDevice);
 }
 
@@ -296,27 +331,12 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
     if (tm) GFD_CK(tm->end(s));                          \
   } while (0)
 
-cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullptr) {
+cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullptr,
+                   bool chains = false) {
   long long L = 0;
   const Tables t{c->tw, c->d2, c->twdf};
   const int plain = c->opts.var_precision == 1 ? 1 : 0;
   GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(c->d_st, 0, sizeof(ImgState) * pl.n, s));
-  for (auto& cl : pl.classes) {
-    GFD_T(GFD_PHASE_SETUP, launch_setup_stats(cl, s));
-    ++L;
-  }
-  for (auto& cl : pl.classes) {
-    GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));
-    L += 2;  // k_setup_init, k_zero_parts
-  }
-  for (auto& cl : pl.classes) {
-    GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
-    // H and Y in double-float, rounded once (they fix the residual of Eq. 10-11)
-    GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_UI, SEL_H, s));
-    GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_Y, SEL_YS, s));
-    GFD_T(GFD_PHASE_SETUP, launch_unpack_dc(cl, s));
-    L += 6;
-  }
   for (int i = 0; i < pl.n; ++i) {
     const gfdeconv_image& u = pl.user[i];
     const size_t bytes = (size_t)u.M * u.N * sizeof(float);
@@ -325,24 +345,65 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     else
       GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(u.u_out, 0, bytes, s));
   }
-  for (int k = 0; k < pl.iters; ++k) {
-    for (auto& cl : pl.classes) {
-      GFD_T(GFD_PHASE_ROW_FWD, launch_row_r2c(cl, t, SEL_U, SEL_S, true, s));
-      GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
-      L += 2;
+  // setup (once per solve) over a list of classes, on stream q
+  auto setup = [&](std::vector<ClassLaunch>& classes, cudaStream_t q) -> cudaError_t {
+    cudaStream_t s = q;  // the GFD_T macro records on `s`
+    for (auto& cl : classes) {
+      GFD_T(GFD_PHASE_SETUP, launch_setup_stats(cl, s));
+      ++L;
     }
-    for (int p = 1; p <= LAMBDA_FALLBACK_PASSES; ++p)
-      for (auto& cl : pl.classes) {
-        GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == LAMBDA_FALLBACK_PASSES, s));
-        ++L;
+    for (auto& cl : classes) {
+      GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));
+      L += 2;  // k_setup_init, k_zero_parts
+    }
+    for (auto& cl : classes) {
+      GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
+      // H and Y in double-float, rounded once (they fix the residual of Eq. 10-11)
+      GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_UI, SEL_H, s));
+      GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_Y, SEL_YS, s));
+      GFD_T(GFD_PHASE_SETUP, launch_unpack_dc(cl, s));
+      L += 6;
+    }
+    return cudaSuccess;
+  };
+  // Steps 1-3 for every iteration over a list of classes, on stream q
+  auto iterate = [&](std::vector<ClassLaunch>& classes, cudaStream_t q) -> cudaError_t {
+    cudaStream_t s = q;  // the GFD_T macro records on `s`
+    for (int k = 0; k < pl.iters; ++k) {
+      for (auto& cl : classes) {
+        GFD_T(GFD_PHASE_ROW_FWD, launch_row_r2c(cl, t, SEL_U, SEL_S, true, s));
+        GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
+        L += 2;
       }
-    for (auto& cl : pl.classes) {
-      GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
-      GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
-                                              1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
-      GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
-      L += 2 + cl.n_rad_groups;  // one guided-filter launch per window radius
+      for (int p = 1; p <= LAMBDA_FALLBACK_PASSES; ++p)
+        for (auto& cl : classes) {
+          GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == LAMBDA_FALLBACK_PASSES, s));
+          ++L;
+        }
+      for (auto& cl : classes) {
+        GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
+        GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
+                                                1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
+        GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
+        L += 2 + cl.n_rad_groups;  // one guided-filter launch per window radius
+      }
     }
+    return cudaSuccess;
+  };
+  if (chains && !tm && CHAINS > 1 && !pl.parts[1].empty()) {
+    GFD_CK(cudaEventRecord(c->ev_fork, s));
+    for (int q = 1; q < CHAINS; ++q) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_fork, 0));
+    GFD_CK(setup(pl.parts[0], s));
+    GFD_CK(iterate(pl.parts[0], s));
+    for (int q = 1; q < CHAINS; ++q) {
+      GFD_CK(setup(pl.parts[q], c->side[q - 1]));
+      GFD_CK(iterate(pl.parts[q], c->side[q - 1]));
+      GFD_CK(cudaEventRecord(c->ev_join[q - 1], c->side[q - 1]));
+      GFD_CK(cudaStreamWaitEvent(s, c->ev_join[q - 1], 0));
+    }
+  } else {
+    GFD_CK(setup(pl.classes, s));
+    GFD_CK(iterate(pl.classes, s));
   }
   for (int i = 0; i < pl.n; ++i) {
     const gfdeconv_image& u = pl.user[i];
@@ -358,7 +419,7 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
 
 cudaError_t capture(gfdeconv_ctx* c, Plan& pl) {
   GFD_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-  const cudaError_t e = record(c, pl, c->cap);
+  const cudaError_t e = record(c, pl, c->cap, nullptr, true);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
   if (e != cudaSuccess) {
@@ -508,10 +569,19 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
       (e = cudaMemcpy(c->d2, d2.data(), sizeof(float) * TAB_ENTRIES, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMalloc(&c->aux_st, sizeof(ImgState))) != cudaSuccess ||
       (e = cudaMemset(c->aux_st, 0, sizeof(ImgState))) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+      (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
     gfdeconv_destroy(c);
     return map_err(e);
   }
+  for (int q = 0; q < CHAINS - 1; ++q) {
+    if ((e = cudaStreamCreateWithFlags(&c->side[q], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming)) != cudaSuccess) {
+      gfdeconv_destroy(c);
+      return map_err(e);
+    }
+  }
+
   *out = c;
   return GFD_OK;
 }
@@ -535,6 +605,11 @@ void gfdeconv_destroy(gfdeconv_ctx* c) {
   if (c->aux_st) cudaFree(c->aux_st);
   if (c->stage) cudaFree(c->stage);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (int q = 0; q < CHAINS - 1; ++q) {
+    if (c->side[q]) cudaStreamDestroy(c->side[q]);
+    if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 

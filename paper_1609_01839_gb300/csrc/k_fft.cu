@@ -686,12 +686,13 @@ static int sm_count() {
 // Persistent grid: as many blocks as fit on the device at once (never more
 // than there are items).
 template <class K>
-static int persistent_grid(K kernel, int threads, size_t smem, int n_items) {
+static int persistent_grid(K kernel, int threads, size_t smem, int n_items, int div = 1) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  const long long g = (long long)per_sm * sm_count();
+  long long g = (long long)per_sm * sm_count();
+  if (div > 1) g = (g + div - 1) / div;
   return (int)(g < n_items ? g : n_items);
 }
 
@@ -757,7 +758,7 @@ static void do_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst, 
   const int n_items = c.cd.n_img * c.cd.M / rpc;
   const int thr = rpc * threads_per_team(L);
   const size_t smem = row_r2c_smem(L, rpc);
-  const int grid = persistent_grid(k_row_r2c<L>, thr, smem, n_items);
+  const int grid = persistent_grid(k_row_r2c<L>, thr, smem, n_items, c.grid_div);
   k_row_r2c<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, src, dst, sum);
 }
 
@@ -778,7 +779,7 @@ static void do_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1
   if (sel1 >= 0) n_items *= 2;
   const int thr = rpc * threads_per_team(L);
   const size_t smem = row_c2r_smem(L, rpc);
-  const int grid = persistent_grid(k_row_c2r<L>, thr, smem, n_items);
+  const int grid = persistent_grid(k_row_c2r<L>, thr, smem, n_items, c.grid_div);
   k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, dsel0, dsel1, scale);
 }
 
@@ -832,7 +833,7 @@ static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, c
   const int nthr = B * threads_per_team(M);
   const size_t smem = col_smem<M>(B, 1, 1, nthr);
   const int n_items = c.cd.n_img * (Lc / B);
-  const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items);
+  const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items, c.grid_div);
   const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M);
   k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, iter, row_items);
 }
@@ -861,7 +862,7 @@ static void do_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t
   const int nthr = B * threads_per_team(M);
   const size_t smem = col_smem<M>(B, 1, 2, 0);
   const int n_items = c.cd.n_img * (Lc / B);
-  const int grid = persistent_grid(k_col_solve_inv<M>, nthr, smem, n_items);
+  const int grid = persistent_grid(k_col_solve_inv<M>, nthr, smem, n_items, c.grid_div);
   k_col_solve_inv<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, t.d2);
 }
 

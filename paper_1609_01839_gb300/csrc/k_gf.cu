@@ -322,12 +322,13 @@ cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, 
                                                       smem) != cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
-    const int warps = per_sm * gf_sm_count() * GFW_WARPS;
+    const int div = c.grid_div > 1 ? c.grid_div : 1;
+    const int warps = (per_sm * gf_sm_count() + div - 1) / div * GFW_WARPS;
     const int strips = (cd.N + gfw_wout(rg.rad) - 1) / gfw_wout(rg.rad);
     int H = cd.M < 64 ? cd.M : 64;
     while (H > 16 && cd.n_img * strips * (cd.M / H) < warps) H /= 2;
     const int n_items = cd.n_img * strips * (cd.M / H);
-    int grid = per_sm * gf_sm_count();
+    int grid = (per_sm * gf_sm_count() + div - 1) / div;
     const int need = (n_items + GFW_WARPS - 1) / GFW_WARPS;
     if (grid > need) grid = need;
     k_guided_filter<<<grid, GFW_WARPS * 32, smem, s>>>(cd, c.imgs, c.st, iter, plain_var, rg.rad, H);

@@ -46,6 +46,7 @@ struct ClassLaunch {
   int max_rad;          // largest guided-filter radius in the class
   int n_rad_groups;
   RadGroup rad_groups[9];
+  int grid_div;         // persistent grids use 1/grid_div of the resident slots (0 = 1)
 };
 
 // Row pass of the 2-D real DFT: real plane src -> packed rows dst.
