@@ -233,6 +233,32 @@ def test_teacher_forced_step_ill_conditioned_lambda(ctx, c2_118_trace, k):
     assert np.abs(u - ref["u"]).max() < U_TOL
 
 
+@pytest.fixture(scope="module")
+def c4_two_steps():
+    """One 4096 x 4096 image of the bandwidth-stress workload (31 x 31 motion
+    blur, BSNR 35, w = 9, eps = 1e-4) and the oracle's first two iterates."""
+    p = S.config_c4_image(0, iters=2)
+    return p, O.solve(p.y, p.h, p.sigma, p.w, p.eps, 2, trace=True)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_teacher_forced_step_4096(ctx, c4_two_steps, k):
+    """Full-size canvas (every pass at its largest tile shapes): one GPU step
+    from the oracle's u_E^k against the oracle's step, element by element."""
+    p, tr = c4_two_steps
+    lam, res, u, uI, up = gpu_step(ctx, p, tr["uE"][k])
+    ref = oracle_step(p, tr["uE"][k])
+    kappa = lambda_condition(p, tr["uE"][k], ref["lam"])
+    record(f"teacher_forced_c4_k{k}", lam_rel=abs(lam / ref["lam"] - 1), kappa=kappa,
+           res_rel=abs(res / ref["res"] - 1), u_max_abs=np.abs(u - ref["u"]).max(),
+           uI_max_abs=np.abs(uI - ref["uI"]).max(), up_max_abs=np.abs(up - ref["up"]).max())
+    assert res == pytest.approx(ref["res"], rel=RES_TOL)
+    assert abs(lam / ref["lam"] - 1) < max(LAM_TOL_TF, kappa * F_REL_ERR), (lam, ref["lam"], kappa)
+    assert np.abs(uI - ref["uI"]).max() < U_TOL
+    assert np.abs(up - ref["up"]).max() < U_TOL
+    assert np.abs(u - ref["u"]).max() < U_TOL
+
+
 # ---------------------------------------------------------------------------
 # Free trajectories of the whole method (Steps 0-3)
 # ---------------------------------------------------------------------------
