@@ -37,9 +37,19 @@ GFD_D df dfs_sub(df a, df b) { return dfs_add(a, df_neg(b)); }
 
 GFD_D cdf cdf_add(cdf a, cdf b) { return cdf{dfs_add(a.re, b.re), dfs_add(a.im, b.im)}; }
 GFD_D cdf cdf_sub(cdf a, cdf b) { return cdf{dfs_sub(a.re, b.re), dfs_sub(a.im, b.im)}; }
+// x1 * y1 + s * x2 * y2 (s = +1 or -1) in double-float: the two leading
+// products exactly (FMA), one two-sum, the cross terms into the low part.
+GFD_D df df_dot2(df x1, df y1, df x2, df y2, float sg) {
+  const float p1 = x1.hi * y1.hi, e1 = fmaf(x1.hi, y1.hi, -p1);
+  const float p2 = sg * (x2.hi * y2.hi), e2 = sg * fmaf(x2.hi, y2.hi, -sg * p2);
+  const df s = two_sum(p1, p2);
+  float lo = s.lo + (e1 + e2);
+  lo = fmaf(x1.hi, y1.lo, fmaf(x1.lo, y1.hi, lo));
+  lo = fmaf(sg * x2.hi, y2.lo, fmaf(sg * x2.lo, y2.hi, lo));
+  return quick_two_sum(s.hi, lo);
+}
 GFD_D cdf cdf_mul(cdf a, cdf b) {
-  return cdf{dfs_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
-             dfs_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+  return cdf{df_dot2(a.re, b.re, a.im, b.im, -1.0f), df_dot2(a.re, b.im, a.im, b.re, 1.0f)};
 }
 GFD_D cdf cdf_half(cdf a) {  // exact
   return cdf{df{0.5f * a.re.hi, 0.5f * a.re.lo}, df{0.5f * a.im.hi, 0.5f * a.im.lo}};

@@ -29,7 +29,7 @@
 namespace gfd {
 
 constexpr int GFW_COLS = 128;   // input columns per strip (4 per lane)
-constexpr int GFW_SUB = 8;      // rows between direct re-formations of the column sums
+constexpr int GFW_SUB = 4;      // rows between direct re-formations of the column sums
 constexpr int GFW_WARPS = 4;    // warps per block
 constexpr int GFW_AHEAD = 2;    // input rows requested ahead of use
 constexpr int GF_RMAX = 8;      // w <= 17
