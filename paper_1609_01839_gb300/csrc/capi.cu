@@ -98,6 +98,8 @@ struct gfdeconv_ctx {
   int aux_next = 0;
   char* stage = nullptr;
   size_t stage_bytes = 0;
+  char* hstage = nullptr;  // pinned host staging of the small per-image arrays
+  size_t hstage_bytes = 0;
 };
 
 namespace {
@@ -604,6 +606,7 @@ void gfdeconv_destroy(gfdeconv_ctx* c) {
   if (c->d_st) cudaFree(c->d_st);
   if (c->aux_st) cudaFree(c->aux_st);
   if (c->stage) cudaFree(c->stage);
+  if (c->hstage) cudaFreeHost(c->hstage);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (int q = 0; q < CHAINS - 1; ++q) {
     if (c->side[q]) cudaStreamDestroy(c->side[q]);
@@ -710,16 +713,27 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
     const gfdeconv_image& im = imgs[i];
     const size_t P = (size_t)im.M * im.N * sizeof(float);
     off_y[i] = take(P);
-    off_h[i] = take((size_t)im.kh * im.kw * sizeof(float));
     off_uo[i] = im.u_orig ? take(P) : 0;
     off_ui[i] = im.u_init ? take(P) : 0;
     off_u[i] = take(P);
-    off_l[i] = im.lambda_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
-    off_is[i] = im.isnr_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
-    off_r[i] = im.res_out ? take(sizeof(double) * (size_t)std::max(iters, 1)) : 0;
     off_I[i] = im.uI_out ? take(P) : 0;
     off_p[i] = im.up_out ? take(P) : 0;
   }
+  // the small arrays back to back: all PSFs, then lambda / ISNR / res of
+  // each image in turn (each pack is one contiguous run on the device)
+  for (int i = 0; i < n; ++i) {
+    off_h[i] = cur;
+    cur += (size_t)imgs[i].kh * imgs[i].kw * sizeof(float);
+  }
+  cur = align256(cur);
+  const size_t itb = sizeof(double) * (size_t)std::max(iters, 1);
+  for (int i = 0; i < n; ++i) {
+    const gfdeconv_image& im = imgs[i];
+    off_l[i] = im.lambda_out ? (cur += itb) - itb : 0;
+    off_is[i] = im.isnr_out ? (cur += itb) - itb : 0;
+    off_r[i] = im.res_out ? (cur += itb) - itb : 0;
+  }
+  cur = align256(cur);
   if (cur > c->stage_bytes) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return map_err(e);
@@ -731,52 +745,110 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
   }
   char* base = c->stage;
   std::vector<gfdeconv_image> dev(imgs, imgs + n);
-  // host->device copies; runs that are contiguous on both sides are merged
+  // The PSFs (in) and the per-iteration lambda / ISNR / residual arrays (out)
+  // are small: they travel packed, one copy each way through pinned host
+  // staging, instead of one copy per image and field.
+  size_t in_small = 0, out_small = 0;
+  const size_t it = sizeof(double) * (size_t)iters;
+  for (int i = 0; i < n; ++i) {
+    in_small += (size_t)imgs[i].kh * imgs[i].kw * sizeof(float);
+    out_small += it * ((imgs[i].lambda_out ? 1 : 0) + (imgs[i].isnr_out ? 1 : 0) + (imgs[i].res_out ? 1 : 0));
+  }
+  const size_t hneed = in_small + out_small;
+  if (hneed > c->hstage_bytes) {
+    if (c->hstage) cudaFreeHost(c->hstage);
+    c->hstage = nullptr;
+    c->hstage_bytes = 0;
+    const cudaError_t e = cudaHostAlloc(&c->hstage, hneed, cudaHostAllocDefault);
+    if (e != cudaSuccess) return map_err(e);
+    c->hstage_bytes = hneed;
+  }
+  // device side of the packs: the h area and the lambda/ISNR/res areas of
+  // the staging are laid out back to back (offsets from the layout above)
   struct Cp {
     char* dst;
     const char* src;
     size_t bytes;
   };
-  std::vector<Cp> h2d, d2h;
+  std::vector<Cp> h2d, d2h, unpack;  // unpack: host pack -> user arrays
+  // One copy per caller buffer: buffers that happen to be adjacent in host
+  // memory may still be separate allocations, and one copy must not span two.
   auto add = [](std::vector<Cp>& v, char* dst, const char* src, size_t bytes) {
+    v.push_back(Cp{dst, src, bytes});
+  };
+  // runs inside this library's own staging (both sides) are merged
+  auto add_run = [](std::vector<Cp>& v, char* dst, const char* src, size_t bytes) {
     if (!v.empty() && v.back().dst + v.back().bytes == dst && v.back().src + v.back().bytes == src)
       v.back().bytes += bytes;
     else
       v.push_back(Cp{dst, src, bytes});
   };
-  const int nf_in = 4;
-  for (int f = 0; f < nf_in; ++f)
-    for (int i = 0; i < n; ++i) {
-      const gfdeconv_image& im = imgs[i];
-      const size_t P = (size_t)im.M * im.N * sizeof(float);
-      if (f == 0) { dev[i].y = (const float*)(base + off_y[i]); add(h2d, base + off_y[i], (const char*)im.y, P); }
-      if (f == 1) { dev[i].h = (const float*)(base + off_h[i]); add(h2d, base + off_h[i], (const char*)im.h, (size_t)im.kh * im.kw * sizeof(float)); }
-      if (f == 2 && im.u_orig) { dev[i].u_orig = (const float*)(base + off_uo[i]); add(h2d, base + off_uo[i], (const char*)im.u_orig, P); }
-      if (f == 3 && im.u_init) { dev[i].u_init = (const float*)(base + off_ui[i]); add(h2d, base + off_ui[i], (const char*)im.u_init, P); }
+  char* hin = c->hstage;
+  char* hout = c->hstage + in_small;
+  size_t pin = 0, pout = 0;
+  std::vector<Cp> small_in_d, small_out_d;  // device areas of the packs, in pack order
+  for (int i = 0; i < n; ++i) {
+    const gfdeconv_image& im = imgs[i];
+    const size_t P = (size_t)im.M * im.N * sizeof(float);
+    const size_t hb = (size_t)im.kh * im.kw * sizeof(float);
+    dev[i].y = (const float*)(base + off_y[i]);
+    add(h2d, base + off_y[i], (const char*)im.y, P);
+    std::memcpy(hin + pin, im.h, hb);
+    dev[i].h = (const float*)(base + off_h[i]);
+    small_in_d.push_back(Cp{base + off_h[i], hin + pin, hb});
+    pin += hb;
+    if (im.u_orig) {
+      dev[i].u_orig = (const float*)(base + off_uo[i]);
+      add(h2d, base + off_uo[i], (const char*)im.u_orig, P);
     }
-  for (int f = 0; f < 6; ++f)
-    for (int i = 0; i < n; ++i) {
-      const gfdeconv_image& im = imgs[i];
-      const size_t P = (size_t)im.M * im.N * sizeof(float);
-      const size_t it = sizeof(double) * (size_t)iters;
-      if (f == 0) { dev[i].u_out = (float*)(base + off_u[i]); add(d2h, (char*)im.u_out, base + off_u[i], P); }
-      if (f == 1 && im.lambda_out) { dev[i].lambda_out = (double*)(base + off_l[i]); if (it) add(d2h, (char*)im.lambda_out, base + off_l[i], it); }
-      if (f == 2 && im.isnr_out) { dev[i].isnr_out = (double*)(base + off_is[i]); if (it) add(d2h, (char*)im.isnr_out, base + off_is[i], it); }
-      if (f == 3 && im.res_out) { dev[i].res_out = (double*)(base + off_r[i]); if (it) add(d2h, (char*)im.res_out, base + off_r[i], it); }
-      if (f == 4 && im.uI_out) { dev[i].uI_out = (float*)(base + off_I[i]); add(d2h, (char*)im.uI_out, base + off_I[i], P); }
-      if (f == 5 && im.up_out) { dev[i].up_out = (float*)(base + off_p[i]); add(d2h, (char*)im.up_out, base + off_p[i], P); }
+    if (im.u_init) {
+      dev[i].u_init = (const float*)(base + off_ui[i]);
+      add(h2d, base + off_ui[i], (const char*)im.u_init, P);
     }
-  for (const Cp& cp : h2d) {
-    const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return map_err(e);
+    dev[i].u_out = (float*)(base + off_u[i]);
+    add(d2h, (char*)im.u_out, base + off_u[i], P);
+    double* const outs[3] = {im.lambda_out, im.isnr_out, im.res_out};
+    const size_t offs[3] = {off_l[i], off_is[i], off_r[i]};
+    double** const douts[3] = {&dev[i].lambda_out, &dev[i].isnr_out, &dev[i].res_out};
+    for (int f = 0; f < 3; ++f) {
+      if (!outs[f]) continue;
+      *douts[f] = (double*)(base + offs[f]);
+      if (it) {
+        small_out_d.push_back(Cp{hout + pout, base + offs[f], it});
+        unpack.push_back(Cp{(char*)outs[f], hout + pout, it});
+        pout += it;
+      }
+    }
+    if (im.uI_out) {
+      dev[i].uI_out = (float*)(base + off_I[i]);
+      add(d2h, (char*)im.uI_out, base + off_I[i], P);
+    }
+    if (im.up_out) {
+      dev[i].up_out = (float*)(base + off_p[i]);
+      add(d2h, (char*)im.up_out, base + off_p[i], P);
+    }
   }
+  // the device areas of each pack are consecutive in the staging layout
+  // (h, then lambda / ISNR / res of each image), so each pack moves in runs
+  std::vector<Cp> h2d_small, d2h_small;
+  for (const Cp& cp : small_in_d) add_run(h2d_small, cp.dst, cp.src, cp.bytes);
+  for (const Cp& cp : small_out_d) add_run(d2h_small, cp.dst, cp.src, cp.bytes);
+  for (const std::vector<Cp>* v : {&h2d_small, &h2d})
+    for (const Cp& cp : *v) {
+      const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return map_err(e);
+    }
   const int r = solve_batched_dev(c, n, dev.data(), iters, s);
   if (r != GFD_OK) return r;
-  for (const Cp& cp : d2h) {
-    const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return map_err(e);
-  }
-  return map_err(cudaStreamSynchronize(s));
+  for (const std::vector<Cp>* v : {&d2h_small, &d2h})
+    for (const Cp& cp : *v) {
+      const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return map_err(e);
+    }
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return map_err(e);
+  for (const Cp& cp : unpack) std::memcpy(cp.dst, cp.src, cp.bytes);
+  return GFD_OK;
 }
 
 int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, int N, int w,
