@@ -242,7 +242,7 @@ class Context:
 
     def make_host_images(self, items, iters):
         """Descriptors for solve_batched_host from dicts of pinned CPU tensors
-        y, h (+ u_orig); allocates pinned outputs u, lam, isnr in the dicts."""
+        y, h (+ u_orig, u_init); allocates pinned outputs u, lam, isnr in the dicts."""
         import torch
         arr = (Image * len(items))()
         for i, it in enumerate(items):
@@ -265,6 +265,7 @@ class Context:
             a.lambda_out = _hptr(it["lam"], "lambda")
             a.isnr_out = _hptr(it["isnr"], "isnr")
             a.u_orig = _hptr(it.get("u_orig"), "u_orig", torch.float32)
+            a.u_init = _hptr(it.get("u_init"), "u_init", torch.float32)
         return arr
 
     def solve_batched_timed(self, arr, iters, stream=None):

@@ -21,8 +21,26 @@ namespace {
 constexpr int AUX_SLOTS = 8;
 constexpr int CHAINS = GFD_CHAINS;
 
+// A host <-> device copy that the host entry point asks a solve to issue.
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
+  cudaMemcpyKind kind;
+};
+
+// Copies around a solve from host buffers: `pre` before everything, per
+// image (user order) `in` before its setup and `out` after its last
+// iteration, `post` after everything.  Recorded into the solve's graph, so
+// that one chain's copies overlap the other chains' work.
+struct HostCopies {
+  std::vector<HostCopy> pre, post;
+  std::vector<std::vector<HostCopy>> in, out;
+};
+
 struct Plan {
   std::vector<unsigned char> key;
+  const HostCopies* copies = nullptr;  // set for the duration of a capture / record
   int n = 0, iters = 0;
   std::vector<int> order;                // internal index -> user index
   std::vector<ClassLaunch> classes;
@@ -338,6 +356,21 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   long long L = 0;
   const Tables t{c->tw, c->d2, c->twdf};
   const int plain = c->opts.var_precision == 1 ? 1 : 0;
+  const HostCopies* hc = pl.copies;
+  auto issue = [&](const std::vector<HostCopy>& v, cudaStream_t q) -> cudaError_t {
+    for (const HostCopy& cp : v) GFD_CK(cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cp.kind, q));
+    return cudaSuccess;
+  };
+  // per-image copies of the images of a list of classes (internal order ->
+  // user order), inputs or outputs
+  auto issue_imgs = [&](std::vector<ClassLaunch>& classes, bool in, cudaStream_t q) -> cudaError_t {
+    if (!hc) return cudaSuccess;
+    for (const ClassLaunch& cl : classes)
+      for (int i = cl.cd.img0; i < cl.cd.img0 + cl.cd.n_img; ++i)
+        GFD_CK(issue(in ? hc->in[pl.order[i]] : hc->out[pl.order[i]], q));
+    return cudaSuccess;
+  };
+  if (hc) GFD_CK(issue(hc->pre, s));
   GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(c->d_st, 0, sizeof(ImgState) * pl.n, s));
   for (int i = 0; i < pl.n; ++i) {
     const gfdeconv_image& u = pl.user[i];
@@ -395,17 +428,23 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   if (chains && !tm && CHAINS > 1 && !pl.parts[1].empty()) {
     GFD_CK(cudaEventRecord(c->ev_fork, s));
     for (int q = 1; q < CHAINS; ++q) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_fork, 0));
+    GFD_CK(issue_imgs(pl.parts[0], true, s));
     GFD_CK(setup(pl.parts[0], s));
     GFD_CK(iterate(pl.parts[0], s));
+    GFD_CK(issue_imgs(pl.parts[0], false, s));
     for (int q = 1; q < CHAINS; ++q) {
+      GFD_CK(issue_imgs(pl.parts[q], true, c->side[q - 1]));
       GFD_CK(setup(pl.parts[q], c->side[q - 1]));
       GFD_CK(iterate(pl.parts[q], c->side[q - 1]));
+      GFD_CK(issue_imgs(pl.parts[q], false, c->side[q - 1]));
       GFD_CK(cudaEventRecord(c->ev_join[q - 1], c->side[q - 1]));
       GFD_CK(cudaStreamWaitEvent(s, c->ev_join[q - 1], 0));
     }
   } else {
+    GFD_CK(issue_imgs(pl.classes, true, s));
     GFD_CK(setup(pl.classes, s));
     GFD_CK(iterate(pl.classes, s));
+    GFD_CK(issue_imgs(pl.classes, false, s));
   }
   for (int i = 0; i < pl.n; ++i) {
     const gfdeconv_image& u = pl.user[i];
@@ -415,6 +454,7 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     if (u.up_out && pl.iters > 0)
       GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.up_out, pl.h_imgs[i].up, bytes, cudaMemcpyDeviceToDevice, s));
   }
+  if (hc) GFD_CK(issue(hc->post, s));
   pl.launches = L;
   return cudaSuccess;
 }
@@ -462,8 +502,31 @@ cudaError_t aux_finish(AuxSlot* a, cudaStream_t s) {
 }
 
 int solve_batched_dev(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
-                      cudaStream_t s) {
+                      cudaStream_t s, const HostCopies* hc = nullptr) {
   std::vector<unsigned char> key = make_key(c, n, imgs, iters);
+  if (hc) {  // the copies are part of the graph: their addresses are part of the key
+    auto put = [&](const std::vector<HostCopy>& v) {
+      auto raw = [&](const void* p, size_t b) {
+        const size_t o = key.size();
+        key.resize(o + b);
+        std::memcpy(key.data() + o, p, b);
+      };
+      const size_t cnt = v.size();
+      raw(&cnt, sizeof(cnt));
+      for (const HostCopy& cp : v) {  // field by field (no padding bytes)
+        const int kind = (int)cp.kind;
+        raw(&cp.dst, sizeof(cp.dst));
+        raw(&cp.src, sizeof(cp.src));
+        raw(&cp.bytes, sizeof(cp.bytes));
+        raw(&kind, sizeof(kind));
+      }
+    };
+    put(hc->pre);
+    put(hc->post);
+    for (const auto& v : hc->in) put(v);
+    for (const auto& v : hc->out) put(v);
+  }
+  c->plan.copies = nullptr;
   if (!(c->have_plan && c->plan.key == key)) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return map_err(e);
@@ -474,7 +537,9 @@ int solve_batched_dev(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int it
       return map_err(e);
     }
     if (c->opts.use_graphs) {
+      c->plan.copies = hc;
       e = capture(c, c->plan);
+      c->plan.copies = nullptr;
       if (e != cudaSuccess) {
         drop_plan(c);
         cudaGetLastError();
@@ -485,10 +550,13 @@ int solve_batched_dev(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int it
     c->have_plan = true;
   }
   cudaError_t e;
-  if (c->opts.use_graphs)
+  if (c->opts.use_graphs) {
     e = cudaGraphLaunch(c->plan.exec, s);
-  else
+  } else {
+    c->plan.copies = hc;
     e = record(c, c->plan, s);
+    c->plan.copies = nullptr;
+  }
   c->last_stream = s;
   c->last_launches = c->plan.launches;
   return map_err(e);
@@ -770,7 +838,7 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
     const char* src;
     size_t bytes;
   };
-  std::vector<Cp> h2d, d2h, unpack;  // unpack: host pack -> user arrays
+  std::vector<Cp> unpack;  // host pack -> user arrays
   // One copy per caller buffer: buffers that happen to be adjacent in host
   // memory may still be separate allocations, and one copy must not span two.
   auto add = [](std::vector<Cp>& v, char* dst, const char* src, size_t bytes) {
@@ -787,26 +855,31 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
   char* hout = c->hstage + in_small;
   size_t pin = 0, pout = 0;
   std::vector<Cp> small_in_d, small_out_d;  // device areas of the packs, in pack order
+  std::vector<std::vector<Cp>> h2d_img(n), d2h_img(n);  // per image (user order)
+  std::vector<Cp> d2h_late;  // u_I, u_p: copied from the staging after the solve's last copies
+  std::vector<Cp> init_in;   // u_init: copied before any of the solve's work
   for (int i = 0; i < n; ++i) {
     const gfdeconv_image& im = imgs[i];
     const size_t P = (size_t)im.M * im.N * sizeof(float);
     const size_t hb = (size_t)im.kh * im.kw * sizeof(float);
     dev[i].y = (const float*)(base + off_y[i]);
-    add(h2d, base + off_y[i], (const char*)im.y, P);
+    add(h2d_img[i], base + off_y[i], (const char*)im.y, P);
     std::memcpy(hin + pin, im.h, hb);
     dev[i].h = (const float*)(base + off_h[i]);
     small_in_d.push_back(Cp{base + off_h[i], hin + pin, hb});
     pin += hb;
     if (im.u_orig) {
       dev[i].u_orig = (const float*)(base + off_uo[i]);
-      add(h2d, base + off_uo[i], (const char*)im.u_orig, P);
+      add(h2d_img[i], base + off_uo[i], (const char*)im.u_orig, P);
     }
     if (im.u_init) {
       dev[i].u_init = (const float*)(base + off_ui[i]);
-      add(h2d, base + off_ui[i], (const char*)im.u_init, P);
+      // before the solve's first work: the start values are copied into u
+      // ahead of every chain
+      init_in.push_back(Cp{base + off_ui[i], (const char*)im.u_init, P});
     }
     dev[i].u_out = (float*)(base + off_u[i]);
-    add(d2h, (char*)im.u_out, base + off_u[i], P);
+    add(d2h_img[i], (char*)im.u_out, base + off_u[i], P);
     double* const outs[3] = {im.lambda_out, im.isnr_out, im.res_out};
     const size_t offs[3] = {off_l[i], off_is[i], off_r[i]};
     double** const douts[3] = {&dev[i].lambda_out, &dev[i].isnr_out, &dev[i].res_out};
@@ -821,11 +894,11 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
     }
     if (im.uI_out) {
       dev[i].uI_out = (float*)(base + off_I[i]);
-      add(d2h, (char*)im.uI_out, base + off_I[i], P);
+      add(d2h_late, (char*)im.uI_out, base + off_I[i], P);
     }
     if (im.up_out) {
       dev[i].up_out = (float*)(base + off_p[i]);
-      add(d2h, (char*)im.up_out, base + off_p[i], P);
+      add(d2h_late, (char*)im.up_out, base + off_p[i], P);
     }
   }
   // the device areas of each pack are consecutive in the staging layout
@@ -833,18 +906,54 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
   std::vector<Cp> h2d_small, d2h_small;
   for (const Cp& cp : small_in_d) add_run(h2d_small, cp.dst, cp.src, cp.bytes);
   for (const Cp& cp : small_out_d) add_run(d2h_small, cp.dst, cp.src, cp.bytes);
-  for (const std::vector<Cp>* v : {&h2d_small, &h2d})
-    for (const Cp& cp : *v) {
-      const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return map_err(e);
+  // With every caller buffer in page-locked memory the copies go into the
+  // solve's graph: each chain of the solve copies its own images in and out,
+  // overlapping the other chains' work.  Otherwise they run before and after.
+  bool pinned = true;
+  for (int i = 0; i < n && pinned; ++i) {
+    const gfdeconv_image& im = imgs[i];
+    const void* bufs[6] = {im.y, im.u_orig, im.u_init, im.u_out, im.uI_out, im.up_out};
+    for (const void* b : bufs) {
+      if (!b) continue;
+      cudaPointerAttributes a{};
+      if (cudaPointerGetAttributes(&a, b) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        pinned = false;
+        break;
+      }
     }
-  const int r = solve_batched_dev(c, n, dev.data(), iters, s);
-  if (r != GFD_OK) return r;
-  for (const std::vector<Cp>* v : {&d2h_small, &d2h})
-    for (const Cp& cp : *v) {
-      const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost, s);
-      if (e != cudaSuccess) return map_err(e);
-    }
+  }
+  HostCopies hc;
+  hc.in.resize(n);
+  hc.out.resize(n);
+  for (const Cp& cp : h2d_small) hc.pre.push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice});
+  for (const Cp& cp : init_in) hc.pre.push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice});
+  for (const Cp& cp : d2h_small) hc.post.push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost});
+  for (int i = 0; i < n; ++i) {
+    for (const Cp& cp : h2d_img[i]) hc.in[i].push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyHostToDevice});
+    for (const Cp& cp : d2h_img[i]) hc.out[i].push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost});
+  }
+  for (const Cp& cp : d2h_late) hc.post.push_back(HostCopy{cp.dst, cp.src, cp.bytes, cudaMemcpyDeviceToHost});
+  if (pinned) {
+    const int r = solve_batched_dev(c, n, dev.data(), iters, s, &hc);
+    if (r != GFD_OK) return r;
+  } else {
+    auto run = [&](const std::vector<HostCopy>& v) -> cudaError_t {
+      for (const HostCopy& cp : v) {
+        const cudaError_t e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cp.kind, s);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    };
+    cudaError_t e = run(hc.pre);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = run(hc.in[i]);
+    if (e != cudaSuccess) return map_err(e);
+    const int r = solve_batched_dev(c, n, dev.data(), iters, s);
+    if (r != GFD_OK) return r;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = run(hc.out[i]);
+    if (e == cudaSuccess) e = run(hc.post);
+    if (e != cudaSuccess) return map_err(e);
+  }
   const cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return map_err(e);
   for (const Cp& cp : unpack) std::memcpy(cp.dst, cp.src, cp.bytes);

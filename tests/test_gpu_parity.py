@@ -350,6 +350,32 @@ def test_batched_host_entry_point(ctx):
         np.testing.assert_allclose(h["isnr"].numpy(), host(d["isnr"]), atol=1e-6)
 
 
+def test_batched_host_entry_point_with_start_values(ctx):
+    """Host buffers with u_init (the start values must reach u before any
+    chain of the solve reads them) and pageable inputs (the path that copies
+    outside the graph) both match the device-buffer solve."""
+    probs = c2_subset()[3:6]
+    iters = 2
+    rng = np.random.default_rng(5)
+    starts = [rng.random(p.shape, dtype=np.float64).astype(np.float32) for p in probs]
+    dev_items = [{"y": cuda(p.y), "h": cuda(p.h), "sigma": p.sigma, "w": p.w, "eps": p.eps,
+                  "u_init": cuda(u0)} for p, u0 in zip(probs, starts)]
+    ctx.solve_batched(dev_items, iters)
+    torch.cuda.synchronize()
+    for pin in (True, False):
+        mk = (lambda a: torch.from_numpy(a).pin_memory()) if pin else (lambda a: torch.from_numpy(a.copy()))
+        host_items = [{"y": mk(p.y), "h": mk(p.h), "sigma": p.sigma, "w": p.w, "eps": p.eps,
+                       "u_init": mk(u0)} for p, u0 in zip(probs, starts)]
+        if not pin:
+            for h in host_items:
+                h["u"] = torch.empty(h["y"].shape, dtype=torch.float32)
+        arr = ctx.make_host_images(host_items, iters)
+        ctx.solve_batched_host_images(arr, iters)
+        for d, h in zip(dev_items, host_items):
+            assert np.abs(host(d["u"]) - h["u"].numpy()).max() < 1e-6, pin
+            np.testing.assert_allclose(h["lam"].numpy(), host(d["lam"]), rtol=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # Edge cases
 # ---------------------------------------------------------------------------
