@@ -108,14 +108,28 @@ k_row_r2c_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __res
   const CdfBuf x{sm, sm + L, sm + 2 * L, sm + 3 * L};
   const int lg = __ffs(L) - 1;
   const float* src = (src_sel == SEL_Y ? d.y : (src_sel == SEL_UI ? d.uI : d.u)) + (size_t)row * N;
+  __shared__ int s_nonzero;
+  if (threadIdx.x == 0) s_nonzero = 0;
+  __syncthreads();
+  bool nz = false;
   for (int n = threadIdx.x; n < L; n += blockDim.x) {
     const float2 v = *reinterpret_cast<const float2*>(src + 2 * n);
+    nz |= (v.x != 0.0f) || (v.y != 0.0f);
     x.put(L == 1 ? 0 : bitrev(n, lg), cdf{df{v.x, 0.0f}, df{v.y, 0.0f}});
   }
+  if (nz) s_nonzero = 1;
   __syncthreads();
-  fft_df(x, L, tab, threadIdx.x, blockDim.x);
   float2* dhi = reinterpret_cast<float2*>(dhi_sel == SEL_S ? d.S : d.QI);
   float2* dlo = reinterpret_cast<float2*>(dlo_sel == SEL_S ? d.S : d.QI);
+  if (!s_nonzero) {  // a zero row (most rows of an embedded PSF) transforms to zero
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+      const size_t o = (size_t)(k / TB) * M * TB + (size_t)row * TB + (k % TB);
+      dhi[o] = make_float2(0.0f, 0.0f);
+      dlo[o] = make_float2(0.0f, 0.0f);
+    }
+    return;
+  }
+  fft_df(x, L, tab, threadIdx.x, blockDim.x);
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
     const cdf Zk = x.get(k);
     cdf X;
