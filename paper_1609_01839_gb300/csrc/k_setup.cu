@@ -1,37 +1,43 @@
 // Once-per-solve kernels: PSF embedding, observation statistics, the
 // discrepancy target (Sec. 3.2, Eq. 12) and the unpacked DC / Nyquist columns.
+#include "df.cuh"
 #include "lambda.cuh"
 #include "launch.h"
 
 namespace gfd {
 
-GFD_D double warp_sum_d(double v) {
+GFD_D df warp_sum_df(df v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
   return v;
 }
 
-// Sum y, y^2, (y - u_orig)^2 over each image (FP64), and sum h, sum |h|.
-// grid (chunks, n_img).
+// Sum y, y^2, (y - u_orig)^2 over each image, and sum h, sum |h|.  The
+// per-thread and per-block sums are double-float (each square formed exactly
+// by a two-product, each difference by a two-sum), so no FP64 instruction
+// runs per pixel; the per-block results are added in FP64.  grid (chunks, n_img).
 __global__ void k_setup_stats(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st) {
-  __shared__ double red[3][32];
+  __shared__ df red[3][32];
   const int gi = cd.img0 + blockIdx.y;
   const ImgDesc& d = imgs[gi];
   const size_t P = (size_t)cd.M * cd.N;
-  double sy = 0.0, syy = 0.0, se = 0.0;
+  df sy{0.0f, 0.0f}, syy{0.0f, 0.0f}, se{0.0f, 0.0f};
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
        i += (size_t)gridDim.x * blockDim.x) {
-    const double v = (double)d.y[i];
-    sy += v;
-    syy += v * v;
+    const float v = __ldg(&d.y[i]);
+    sy = df_add(sy, df_make(v));
+    syy = df_add(syy, two_prod(v, v));
     if (d.uo) {
-      const double e = v - (double)d.uo[i];
-      se += e * e;
+      const df e = two_sum(v, -__ldg(&d.uo[i]));  // exact difference
+      df e2 = two_prod(e.hi, e.hi);
+      e2.lo = fmaf(2.0f * e.hi, e.lo, e2.lo);
+      se = df_add(se, quick_two_sum(e2.hi, e2.lo));
     }
   }
-  sy = warp_sum_d(sy);
-  syy = warp_sum_d(syy);
-  se = warp_sum_d(se);
+  sy = warp_sum_df(sy);
+  syy = warp_sum_df(syy);
+  se = warp_sum_df(se);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][warp] = sy;
@@ -40,15 +46,15 @@ __global__ void k_setup_stats(ClassDesc cd, const ImgDesc* __restrict__ imgs, Im
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += red[0][w];
-      b += red[1][w];
-      c += red[2][w];
+    df a = red[0][0], b = red[1][0], c = red[2][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      a = df_add(a, red[0][w]);
+      b = df_add(b, red[1][w]);
+      c = df_add(c, red[2][w]);
     }
-    atomicAdd(&st[gi].sum_y, a);
-    atomicAdd(&st[gi].sum_yy, b);
-    if (d.uo) atomicAdd(&st[gi].den_isnr, c);
+    atomicAdd(&st[gi].sum_y, df_to_double(a));
+    atomicAdd(&st[gi].sum_yy, df_to_double(b));
+    if (d.uo) atomicAdd(&st[gi].den_isnr, df_to_double(c));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double sh = 0.0, sa = 0.0;
