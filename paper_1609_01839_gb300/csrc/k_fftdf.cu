@@ -76,20 +76,67 @@ struct CdfBuf {
   }
 };
 
-// In-place radix-2 DIT transform of length L (input already bit-reversed)
-// by `nt` threads with index t; synchronises the block after every stage.
-GFD_D void fft_df(const CdfBuf& x, int L, const float4* __restrict__ tab, int t, int nt) {
-  for (int half = 1; half < L; half <<= 1) {
-    const int step = L / (2 * half);  // W_{2 half}^j = W_L^(j * step)
-    for (int b = t; b < L / 2; b += nt) {
-      const int j = b & (half - 1);
-      const int k = ((b - j) << 1) + j;
-      const cdf w = tw_df(tab, L, j * step);
-      const cdf u = x.get(k);
-      const cdf v = cdf_mul(w, x.get(k + half));
-      x.put(k, cdf_add(u, v));
-      x.put(k + half, cdf_sub(u, v));
-    }
+GFD_D cdf cdf_mul_negi(cdf a) { return cdf{a.im, df_neg(a.re)}; }  // -i a, exact
+
+// Two consecutive radix-2 DIT stages (half sizes h and 2h) on the four
+// points k, k+h, k+2h, k+3h, k = 4 (q - j) + j with j = q mod h.  The
+// second stage's twiddle for the odd pair is W_4h^(j+h) = -i W_4h^j, so one
+// twiddle product is replaced by an exact multiplication by -i; for h = 1
+// every twiddle is 1 and no product is formed.
+GFD_D void df_radix4(const CdfBuf& x, int L, int h, const float4* __restrict__ tab, int q) {
+  const int j = q & (h - 1);
+  const int k = ((q - j) << 2) + j;
+  const cdf a0 = x.get(k), a1 = x.get(k + h), a2 = x.get(k + 2 * h), a3 = x.get(k + 3 * h);
+  cdf b0, b1, b2, b3;
+  if (h == 1) {
+    b0 = cdf_add(a0, a1);
+    b1 = cdf_sub(a0, a1);
+    b2 = cdf_add(a2, a3);
+    b3 = cdf_sub(a2, a3);
+  } else {
+    const cdf w1 = tw_df(tab, L, j * (L / (2 * h)));  // W_2h^j
+    const cdf v1 = cdf_mul(w1, a1), v3 = cdf_mul(w1, a3);
+    b0 = cdf_add(a0, v1);
+    b1 = cdf_sub(a0, v1);
+    b2 = cdf_add(a2, v3);
+    b3 = cdf_sub(a2, v3);
+  }
+  cdf v2 = b2, v4 = cdf_mul_negi(b3);
+  if (h > 1) {
+    const cdf w2 = tw_df(tab, L, j * (L / (4 * h)));  // W_4h^j
+    v2 = cdf_mul(w2, b2);
+    v4 = cdf_mul_negi(cdf_mul(w2, b3));
+  }
+  x.put(k, cdf_add(b0, v2));
+  x.put(k + 2 * h, cdf_sub(b0, v2));
+  x.put(k + h, cdf_add(b1, v4));
+  x.put(k + 3 * h, cdf_sub(b1, v4));
+}
+
+GFD_D void df_radix2(const CdfBuf& x, int L, int h, const float4* __restrict__ tab, int q) {
+  const int j = q & (h - 1);
+  const int k = ((q - j) << 1) + j;
+  const cdf u = x.get(k);
+  const cdf v = cdf_mul(tw_df(tab, L, j * (L / (2 * h))), x.get(k + h));
+  x.put(k, cdf_add(u, v));
+  x.put(k + h, cdf_sub(u, v));
+}
+
+// In-place DIT transform of length L (input already bit-reversed) by `nt`
+// threads with index t: radix-4 steps, one radix-2 stage last when log2 L is
+// odd; synchronises the block after every step.  `active` threads take part
+// in the arithmetic, all of them in the barriers.
+GFD_D void fft_df(const CdfBuf& x, int L, const float4* __restrict__ tab, int t, int nt,
+                  bool active = true) {
+  int h = 1;
+  for (; 4 * h <= L; h *= 4) {
+    if (active)
+      for (int q = t; q < L / 4; q += nt) df_radix4(x, L, h, tab, q);
+    __syncthreads();
+  }
+  if (h < L) {
+    if (active)
+      for (int q = t; q < L / 2; q += nt) df_radix2(x, L, h, tab, q);
     __syncthreads();
   }
 }
@@ -176,21 +223,7 @@ k_col_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __restric
   const int per = blockDim.x / TB;
   const int b = threadIdx.x / per, tt = threadIdx.x - b * per;
   const CdfBuf x{sm + b * 4 * M, sm + b * 4 * M + M, sm + b * 4 * M + 2 * M, sm + b * 4 * M + 3 * M};
-  for (int half = 1; half < M; half <<= 1) {
-    const int step = M / (2 * half);
-    if (b < TB) {
-      for (int q = tt; q < M / 2; q += per) {
-        const int j = q & (half - 1);
-        const int k = ((q - j) << 1) + j;
-        const cdf w = tw_df(tab, M, j * step);
-        const cdf u = x.get(k);
-        const cdf v = cdf_mul(w, x.get(k + half));
-        x.put(k, cdf_add(u, v));
-        x.put(k + half, cdf_sub(u, v));
-      }
-    }
-    __syncthreads();
-  }
+  fft_df(x, M, tab, tt, per, b < TB);
   for (int e = threadIdx.x; e < M * TB; e += blockDim.x) {
     const int m = e / TB, bb = e - m * TB;
     const CdfBuf y{sm + bb * 4 * M, sm + bb * 4 * M + M, sm + bb * 4 * M + 2 * M,
@@ -216,12 +249,12 @@ cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* tab, int src,
                                cudaStream_t s) {
   (void)df_sm_count;
   const int M = c.cd.M, L = c.cd.N / 2, TB = c.cd.TB;
-  const int rthreads = L / 2 < 256 ? (L / 2 < 32 ? 32 : L / 2) : 256;
+  const int rthreads = L / 4 < 256 ? (L / 4 < 32 ? 32 : L / 4) : 256;
   k_row_r2c_df<<<c.cd.n_img * M, rthreads, (size_t)4 * L * sizeof(float), s>>>(
       c.cd, c.imgs, tab, src, SEL_S, SEL_QI);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int per = M / 2 < 64 ? M / 2 : 64;
+  int per = M / 4 < 64 ? M / 4 : 64;
   if (per < 1) per = 1;
   int cthreads = per * TB;
   if (cthreads > 512) cthreads = 512 - 512 % TB;
