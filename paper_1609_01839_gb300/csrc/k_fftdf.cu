@@ -61,14 +61,26 @@ GFD_D cdf tw_df(const float4* __restrict__ tab, int L, int m) {
   return cdf{df{v.x, v.y}, df{v.z, v.w}};
 }
 
-// Shared buffer of one transform: hi and lo planes of re and im.
+// Shared buffer of one transform: hi and lo planes of re and im, each of
+// padded length df_plane(L).  Element i sits at i + i/32, so the bit-reversed
+// scatter (consecutive i land L/2 apart) and the small-stride butterfly
+// steps spread over the banks.
+GFD_HD int df_plane(int L) { return L + (L >> 5); }
 struct CdfBuf {
   float* rh;
   float* rl;
   float* ih;
   float* il;
-  GFD_D cdf get(int i) const { return cdf{df{rh[i], rl[i]}, df{ih[i], il[i]}}; }
+  GFD_D static CdfBuf at(float* base, int L) {
+    const int p = df_plane(L);
+    return CdfBuf{base, base + p, base + 2 * p, base + 3 * p};
+  }
+  GFD_D cdf get(int i) const {
+    i += i >> 5;
+    return cdf{df{rh[i], rl[i]}, df{ih[i], il[i]}};
+  }
   GFD_D void put(int i, cdf v) const {
+    i += i >> 5;
     rh[i] = v.re.hi;
     rl[i] = v.re.lo;
     ih[i] = v.im.hi;
@@ -152,7 +164,7 @@ k_row_r2c_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __res
   const int M = cd.M, N = cd.N, L = N / 2, TB = cd.TB;
   const int li = blockIdx.x / M, row = blockIdx.x - li * M;
   const ImgDesc& d = imgs[cd.img0 + li];
-  const CdfBuf x{sm, sm + L, sm + 2 * L, sm + 3 * L};
+  const CdfBuf x = CdfBuf::at(sm, L);
   const int lg = __ffs(L) - 1;
   const float* src = (src_sel == SEL_Y ? d.y : (src_sel == SEL_UI ? d.uI : d.u)) + (size_t)row * N;
   __shared__ int s_nonzero;
@@ -196,6 +208,10 @@ k_row_r2c_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __res
   }
 }
 
+// Floats per column buffer of the column pass: four padded planes and one
+// word of skew, so that the columns of a tile start in different banks.
+GFD_HD int df_col_stride(int M) { return 4 * df_plane(M) + 1; }
+
 // Column pass: packed rows (hi in plane shi, lo in plane slo) -> complex
 // column transforms rounded once into plane dst.  One block per tile of TB
 // columns; threads split over the tile's columns.
@@ -208,6 +224,7 @@ k_col_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __restric
   const int li = blockIdx.x / tiles, t = blockIdx.x - li * tiles;
   const ImgDesc& d = imgs[cd.img0 + li];
   const int lg = __ffs(M) - 1;
+  const int cstride = df_col_stride(M);
   const size_t off = (size_t)t * M * TB;
   const float2* shi = reinterpret_cast<const float2*>(shi_sel == SEL_S ? d.S : d.QI) + off;
   const float2* slo = reinterpret_cast<const float2*>(slo_sel == SEL_S ? d.S : d.QI) + off;
@@ -215,19 +232,18 @@ k_col_df(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float4* __restric
   for (int e = threadIdx.x; e < M * TB; e += blockDim.x) {
     const int m = e / TB, b = e - m * TB;
     const float2 h = shi[e], l = slo[e];
-    const CdfBuf x{sm + b * 4 * M, sm + b * 4 * M + M, sm + b * 4 * M + 2 * M, sm + b * 4 * M + 3 * M};
+    const CdfBuf x = CdfBuf::at(sm + b * cstride, M);
     x.put(M == 1 ? 0 : bitrev(m, lg), cdf{df{h.x, l.x}, df{h.y, l.y}});
   }
   __syncthreads();
   // threads per column: the block's threads split evenly over the TB columns
   const int per = blockDim.x / TB;
   const int b = threadIdx.x / per, tt = threadIdx.x - b * per;
-  const CdfBuf x{sm + b * 4 * M, sm + b * 4 * M + M, sm + b * 4 * M + 2 * M, sm + b * 4 * M + 3 * M};
+  const CdfBuf x = CdfBuf::at(sm + b * cstride, M);
   fft_df(x, M, tab, tt, per, b < TB);
   for (int e = threadIdx.x; e < M * TB; e += blockDim.x) {
     const int m = e / TB, bb = e - m * TB;
-    const CdfBuf y{sm + bb * 4 * M, sm + bb * 4 * M + M, sm + bb * 4 * M + 2 * M,
-                   sm + bb * 4 * M + 3 * M};
+    const CdfBuf y = CdfBuf::at(sm + bb * cstride, M);
     const cdf v = y.get(m);
     dst[e] = make_float2(v.re.hi + v.re.lo, v.im.hi + v.im.lo);
   }
@@ -250,7 +266,7 @@ cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* tab, int src,
   (void)df_sm_count;
   const int M = c.cd.M, L = c.cd.N / 2, TB = c.cd.TB;
   const int rthreads = L / 4 < 256 ? (L / 4 < 32 ? 32 : L / 4) : 256;
-  k_row_r2c_df<<<c.cd.n_img * M, rthreads, (size_t)4 * L * sizeof(float), s>>>(
+  k_row_r2c_df<<<c.cd.n_img * M, rthreads, (size_t)4 * df_plane(L) * sizeof(float), s>>>(
       c.cd, c.imgs, tab, src, SEL_S, SEL_QI);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -259,7 +275,7 @@ cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* tab, int src,
   int cthreads = per * TB;
   if (cthreads > 512) cthreads = 512 - 512 % TB;
   if (cthreads < TB) cthreads = TB;
-  const size_t smem = (size_t)TB * 4 * M * sizeof(float);
+  const size_t smem = (size_t)TB * df_col_stride(M) * sizeof(float);
   k_col_df<<<c.cd.n_img * (L / TB), cthreads, smem, s>>>(c.cd, c.imgs, tab, SEL_S, SEL_QI,
                                                         dst == SEL_H ? SEL_H : SEL_YS);
   return cudaGetLastError();
