@@ -11,24 +11,27 @@
 //   accumulating the per-bin terms in FP32 per thread and in FP64 across
 //   warps and blocks; one warp of the image's last block then updates the
 //   bracket.  Wide brackets use geometric nodes and are narrowed to the pair
-//   of nodes that straddles T.  Brackets of ratio <= 1.6 use Chebyshev-
-//   Lobatto nodes in lambda: f is analytic around such a bracket (its poles
-//   lie at lambda = -|H_b|^2 <= 0), so the degree-11 interpolant through the
-//   node values is exact to ~1e-12 relative, and its root is the answer.
-//   Node values are rounded to FP32 and used as the exact abscissae; the
-//   interpolant is evaluated in double-float arithmetic (FP64 is slow on
-//   this part), and its root is located by multisection with one trial
-//   point per lane, which needs only the sign of the interpolant.
+//   of nodes that straddles T.  Brackets of ratio <= 4 use Chebyshev-
+//   Lobatto nodes in t = ln(lambda): as a function of t, f is analytic in
+//   the strip |Im t| < pi (its poles lie at lambda = -|H_b|^2 <= 0, i.e.
+//   t = ln|H_b|^2 + i pi), whatever the spectrum, so the degree-11
+//   interpolant in t through the node values has its root within ~1e-10
+//   relative of the true one on a bracket of ratio 4 (~1e-14 on ratio 1.6).
+//   Node values are rounded to FP32; their logarithms, formed once in FP64,
+//   are the exact abscissae.  The interpolant is evaluated in double-float
+//   arithmetic (FP64 is slow on this part), and its root is located by
+//   multisection with one trial point per lane, which needs only the sign
+//   of the interpolant.
 // The first pass of each iteration is fused into the forward column FFT and
-// uses the bracket [lambda_{k-1}/1.25, 1.25 lambda_{k-1}].
+// uses a bracket of ratio 4 around an extrapolation of the previous lambdas.
 #pragma once
 #include "common.cuh"
 #include "df.cuh"
 
 namespace gfd {
 
-constexpr float INTERP_RATIO = 1.6f;   // largest bracket ratio interpolated
-constexpr float PRIMARY_RATIO = 1.25f;  // primary bracket: [lam/1.25, 1.25 lam]
+constexpr float INTERP_RATIO = 4.0f;   // largest bracket ratio interpolated
+constexpr float PRIMARY_RATIO = 2.0f;  // primary bracket: [c/2, 2 c]
 constexpr float INITIAL_LO = 1e-8f, INITIAL_HI = 1e4f;
 constexpr int MODE_GEOM = 0, MODE_CHEB = 1;
 
@@ -42,10 +45,8 @@ __device__ constexpr float kLobatto[KNODES] = {
 GFD_D float bracket_node(float lo, float hi, int mode, int j) {
   if (j == 0) return lo;
   if (j == KNODES - 1) return hi;
-  if (mode == MODE_CHEB) {
-    const float c = 0.5f * (lo + hi), h = 0.5f * (hi - lo);
-    return c - h * kLobatto[j];
-  }
+  if (mode == MODE_CHEB)  // Chebyshev-Lobatto in ln(lambda)
+    return lo * exp2f(0.5f * (1.0f - kLobatto[j]) * log2f(hi / lo));
   return lo * exp2f((float)j / (KNODES - 1) * log2f(hi / lo));
 }
 
@@ -207,40 +208,45 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
   return last;
 }
 
-// Root of the interpolant through (x_m, g_m), m < KNODES (x ascending FP32
-// values used as exact abscissae, g increasing through 0 between x_j and
-// x_{j+1}).  Lane m < KNODES holds (x_m, g_m).  Barycentric weights and the
-// interpolant are formed in double-float; the root is bracketed by
-// multisection: every lane evaluates the sign of the interpolant at its own
-// trial point, and the bracket shrinks 33-fold per round.  Returns lambda.
+// Root of the interpolant in t = ln(lambda) through (t_m, g_m), m < KNODES,
+// t_m = ln(x_m) of the FP32 node values x_m (ascending; g increasing through
+// 0 between x_j and x_{j+1}).  Lane m < KNODES holds (x_m, g_m).  The
+// logarithms are formed in FP64 and carried as double-float; barycentric
+// weights and the interpolant are formed in double-float; the root is
+// bracketed by multisection: every lane evaluates the sign of the
+// interpolant at its own trial point, and the bracket shrinks 33-fold per
+// round.  Returns lambda = exp(t_root).
 GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
   const bool own = lane < KNODES;
+  const df tm = own ? df_from_double(log((double)xm)) : df_make(0.0f);
   // All abscissa differences are scaled by a power of two ~ 1/(bracket
   // width): exact, and it keeps the products of 11 differences in FP32
   // range (the barycentric ratio does not depend on the scale).
-  const float x0 = __shfl_sync(0xffffffffu, xm, 0);
-  const float xK = __shfl_sync(0xffffffffu, xm, KNODES - 1);
+  const float t0 = __shfl_sync(0xffffffffu, tm.hi, 0);
+  const float tK = __shfl_sync(0xffffffffu, tm.hi, KNODES - 1);
   int ex;
-  frexpf(xK - x0, &ex);
+  frexpf(tK - t0, &ex);
   const float sc = ldexpf(1.0f, -ex);
-  // weight w_m = 1 / prod_{n != m} (x_m - x_n); the differences are exact
-  // (Sterbenz: the nodes lie within a factor 1.6 of each other)
+  // weight w_m = 1 / prod_{n != m} (t_m - t_n), differences in double-float
   df prod = df_make(1.0f);
   for (int n = 0; n < KNODES; ++n) {
-    const float xn = __shfl_sync(0xffffffffu, xm, n);
-    if (own && n != lane) prod = df_mul_f(prod, (xm - xn) * sc);
+    const df tn{__shfl_sync(0xffffffffu, tm.hi, n), __shfl_sync(0xffffffffu, tm.lo, n)};
+    if (own && n != lane) {
+      const df dd = df_sub(tm, tn);
+      prod = df_mul(prod, df{dd.hi * sc, dd.lo * sc});
+    }
   }
   const df w = own ? df_rcp(prod) : df_make(0.0f);
-  __shared__ float s_x[KNODES], s_g[KNODES];
-  __shared__ df s_w[KNODES];
+  __shared__ df s_t[KNODES], s_w[KNODES];
+  __shared__ float s_g[KNODES];
   if (own) {
-    s_x[lane] = xm;
+    s_t[lane] = tm;
     s_g[lane] = gm;
     s_w[lane] = w;
   }
   __syncwarp();
-  df a = df_make(s_x[j]), b = df_make(s_x[j + 1]);
-  for (int round = 0; round < 7; ++round) {
+  df a = s_t[j], b = s_t[j + 1];
+  for (int round = 0; round < 8; ++round) {
     // trial point a + (b - a) (lane + 1) / 33
     const df width = df_sub(b, a);
     const df t = df_add(a, df_mul_f(width, (float)(lane + 1) / 33.0f));
@@ -248,7 +254,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
     bool at_node = false;
     float node_g = 0.0f;
     for (int m = 0; m < KNODES; ++m) {
-      const df dd = df_sub(t, df_make(s_x[m]));
+      const df dd = df_sub(t, s_t[m]);
       if (dd.hi == 0.0f) {
         at_node = true;
         node_g = s_g[m];
@@ -267,9 +273,9 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
     const df nbv = nb < 32 ? df_add(a, df_mul_f(width, (float)(nb + 1) / 33.0f)) : b;
     a = na;
     b = nbv;
-    if (df_to_double(df_sub(b, a)) <= 1e-12 * (double)s_x[j]) break;
+    if (df_to_double(df_sub(b, a)) <= 1e-13) break;  // absolute in t: relative in lambda
   }
-  return 0.5 * (df_to_double(a) + df_to_double(b));
+  return exp(0.5 * (df_to_double(a) + df_to_double(b)));
 }
 
 // Record lambda_k and set the bracket of iteration k+1's fused first pass.
@@ -277,7 +283,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
 // the second and by 1/8..8 to the third; later it changes smoothly, so the
 // bracket is centred on the extrapolation lambda_k (lambda_k / lambda_{k-1})
 // (ratio clamped to [1/2, 2]).  The first two use geometric nodes, resolved by
-// one more pass; the later ones are narrow enough (ratio 1.5625) for the
+// one more pass; the later ones are narrow enough (ratio 4) for the
 // interpolation to resolve them in the fused pass itself.
 GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int lane) {
   if (lane == 0) {
