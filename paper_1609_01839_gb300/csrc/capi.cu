@@ -275,6 +275,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
       d.h = im.h;
       d.u = im.u_out;
       d.uo = im.u_orig;
+      d.u0 = im.u_init;
       d.lam_out = im.lambda_out;
       d.isnr_out = im.isnr_out;
       d.res_out = im.res_out;
@@ -372,20 +373,13 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   };
   if (hc) GFD_CK(issue(hc->pre, s));
   GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(c->d_st, 0, sizeof(ImgState) * pl.n, s));
-  for (int i = 0; i < pl.n; ++i) {
-    const gfdeconv_image& u = pl.user[i];
-    const size_t bytes = (size_t)u.M * u.N * sizeof(float);
-    if (u.u_init)
-      GFD_T(GFD_PHASE_COPY, cudaMemcpyAsync(u.u_out, u.u_init, bytes, cudaMemcpyDeviceToDevice, s));
-    else
-      GFD_T(GFD_PHASE_COPY, cudaMemsetAsync(u.u_out, 0, bytes, s));
-  }
   // setup (once per solve) over a list of classes, on stream q
   auto setup = [&](std::vector<ClassLaunch>& classes, cudaStream_t q) -> cudaError_t {
     cudaStream_t s = q;  // the GFD_T macro records on `s`
     for (auto& cl : classes) {
+      GFD_T(GFD_PHASE_COPY, launch_init_u(cl, s));  // u_E = u_init or 0
       GFD_T(GFD_PHASE_SETUP, launch_setup_stats(cl, s));
-      ++L;
+      L += 2;
     }
     for (auto& cl : classes) {
       GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));

@@ -106,6 +106,7 @@ struct ImgDesc {
   const float* h;     // kh*kw
   float* u;           // M*N, the iterate (caller's output buffer)
   const float* uo;    // M*N or null
+  const float* u0;    // starting u_E, M*N, or null (u_E = 0)
   double* lam_out;    // [iters] or null
   double* isnr_out;   // [iters] or null
   double* res_out;    // [iters] or null

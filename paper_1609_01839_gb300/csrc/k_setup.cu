@@ -68,6 +68,22 @@ __global__ void k_setup_stats(ClassDesc cd, const ImgDesc* __restrict__ imgs, Im
   }
 }
 
+// Starting iterate of every image of a class: u_E = u_init, or 0 (Step 0).
+// Images are M*N floats, 16-byte aligned, M*N a multiple of 4 for every
+// supported canvas; grid-stride over float4 groups of all images.
+__global__ void k_init_u(ClassDesc cd, const ImgDesc* __restrict__ imgs) {
+  const size_t P4 = (size_t)cd.M * cd.N / 4;
+  const size_t total = P4 * cd.n_img;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t li = idx / P4, i = idx - li * P4;
+    const ImgDesc& d = imgs[cd.img0 + li];
+    const float4 v = d.u0 ? __ldg(reinterpret_cast<const float4*>(d.u0) + i)
+                          : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    reinterpret_cast<float4*>(d.u)[i] = v;
+  }
+}
+
 // rho (Eq. 12), the target T = rho P sigma^2 (Sec. 3.2), the first bracket.
 __global__ void k_setup_init(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                              double rho_fixed) {
@@ -172,6 +188,15 @@ cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
   int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));
   if (chunks > 64) chunks = 64;
   k_setup_stats<<<dim3(chunks, c.cd.n_img), 256, 0, s>>>(c.cd, c.imgs, c.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_u(const ClassLaunch& c, cudaStream_t s) {
+  const size_t total = (size_t)c.cd.M * c.cd.N / 4 * c.cd.n_img;
+  size_t nb = (total + 255) / 256;
+  if (nb > 152 * 16) nb = 152 * 16;
+  if (nb < 1) nb = 1;
+  k_init_u<<<(unsigned)nb, 256, 0, s>>>(c.cd, c.imgs);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* twdf, int src
                                cudaStream_t s);
 // Setup kernels.
 cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s);
+cudaError_t launch_init_u(const ClassLaunch& c, cudaStream_t s);
 cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s);
 cudaError_t launch_embed_psf(const ClassLaunch& c, int dst, cudaStream_t s);
 cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s);
