@@ -72,6 +72,19 @@ GFD_D void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16), split into pieces of at most 16 KB issued by the lanes of
+// warp 0.  No completion to wait for: later loads simply find the lines in L2.
+GFD_D void prefetch_l2(const void* p, unsigned int bytes) {
+  constexpr unsigned int PIECE = 16384;
+  if (threadIdx.x >= 32) return;
+  for (unsigned int o = threadIdx.x * PIECE; o < bytes; o += 32 * PIECE) {
+    const unsigned int n = bytes - o < PIECE ? bytes - o : PIECE;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"((const char*)p + o), "r"(n)
+                 : "memory");
+  }
+}
+
 // Per-image solver state, one per image of a batch, in device memory.
 struct ImgState {
   double T;          // discrepancy target rho * P * sigma^2 (Sec. 3.2)

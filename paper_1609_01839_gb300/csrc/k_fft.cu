@@ -340,6 +340,9 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
       issue_tile(landS, d.S + off, M, B, B);
+      // H and Y of the item are read after its transform: start them now
+      prefetch_l2(d.H + off, (unsigned int)(tile * sizeof(float2)));
+      prefetch_l2(d.Y + off, (unsigned int)(tile * sizeof(float2)));
     }
     cp_async_commit();
   };
@@ -601,6 +604,8 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
       issue_tile(landU, d.S + off, M, B, B);
+      prefetch_l2(d.H + off, (unsigned int)(tile * sizeof(float2)));
+      prefetch_l2(d.Y + off, (unsigned int)(tile * sizeof(float2)));
     }
     cp_async_commit();
   };
