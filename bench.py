@@ -271,7 +271,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup,
-                              "ms_per_step": ms_max / args.steps, "only_solve": True}), flush=True)
+                              "ms_per_step": ms_max / args.steps, "only_solve": True,
+                              "gpu_launches_per_step": launches_per_step}), flush=True)
         ctx.close()
         if dist is not None:
             dist.destroy_process_group()
