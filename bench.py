@@ -109,7 +109,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # side files (clock samples) go to $GFD_ARTIFACT_DIR, default ./artifacts
+        out = os.environ.get("GFD_ARTIFACT_DIR", os.path.join(ROOT, "artifacts"))
+        self.path = os.path.join(out, f"clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:

@@ -48,7 +48,9 @@ def ctx():
 def record(name, **vals):
     import json
     import os
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    # per-test error figures go to $GFD_ARTIFACT_DIR, default <repo>/artifacts
+    d = os.environ.get("GFD_ARTIFACT_DIR") or os.path.join(
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "artifacts")
     try:
         os.makedirs(d, exist_ok=True)
         with open(os.path.join(d, "parity_metrics.jsonl"), "a") as f:
