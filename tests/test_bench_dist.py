@@ -59,3 +59,17 @@ def test_single_process_reductions_are_identity():
     assert bench.reduce_max(3.5) == 3.5
     assert bench.reduce_sum(2.0) == 2.0
     assert bench.shard_indices(0, 1) == list(range(bench.N_IMAGES))
+
+
+def test_median_step_seconds_ignores_a_one_off_stall():
+    import time
+    calls = []
+
+    def step():
+        calls.append(1)
+        time.sleep(0.06 if len(calls) == 2 else 0.002)  # one stall in the first run
+
+    synced = []
+    t = bench.median_step_seconds(step, steps=5, reps=3, sync=lambda: synced.append(1))
+    assert len(calls) == 15 and len(synced) == 3
+    assert 0.0015 < t < 0.008  # the stalled run (~14 ms per step) is not the median
