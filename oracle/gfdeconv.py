@@ -168,7 +168,33 @@ def box_mean(x, w):
     return outer / (w * w)
 
 
-def guided_filter(uI, up, w, eps):
+def box_mean_truncated(x, w):
+    """Window mean with the w x w window cut at the canvas edge: the sum of
+    the window's pixels that lie inside the canvas divided by their number.
+    reading: the non-periodic boundary of He et al.'s box filter, which the
+    paper cites for its O(N^2) guided filter (Sec. 3.1); an opt-in variant of
+    the periodic windows above.  Written as the sum over the window's
+    offsets of the zero-extended image, divided by the same sum of ones."""
+    if w % 2 != 1 or w < 1:
+        raise ValueError("w must be odd and positive")
+    rad = (w - 1) // 2
+    x = np.asarray(x, dtype=np.float64)
+    M, N = x.shape
+    xz = np.pad(x, rad)                       # zero outside the canvas
+    oz = np.pad(np.ones((M, N)), rad)
+    total = np.zeros((M, N))
+    count = np.zeros((M, N))
+    for dy in range(-rad, rad + 1):
+        for dx in range(-rad, rad + 1):
+            total += xz[rad + dy:rad + dy + M, rad + dx:rad + dx + N]
+            count += oz[rad + dy:rad + dy + M, rad + dx:rad + dx + N]
+    return total / count
+
+
+BOX_MEANS = {"periodic": box_mean, "truncated": box_mean_truncated}
+
+
+def guided_filter(uI, up, w, eps, boundary="periodic"):
     """u = guidfilter(u_I, u_p, w, eps) (Sec. 2):
     a_k = (mean_w(u_I u_p) - mu_k pbar_k) / (sigma_k^2 + eps)   (Eq. 3)
     b_k = pbar_k - a_k mu_k                                      (Eq. 4)
@@ -176,15 +202,18 @@ def guided_filter(uI, up, w, eps):
     with mu_k, pbar_k the window means of u_I, u_p and sigma_k^2 the window
     (population) variance of u_I (reading of "mean and variance").
     The filter output averages a and b over the windows covering each pixel
-    (reading of Eq. 5's garbled index: the window centred at i)."""
+    (reading of Eq. 5's garbled index: the window centred at i).
+    ``boundary`` selects periodic windows (default) or windows truncated at
+    the canvas edge (box_mean_truncated); Eq. 3-5 are the same for both."""
+    box = BOX_MEANS[boundary]
     uI = np.asarray(uI, dtype=np.float64)
     up = np.asarray(up, dtype=np.float64)
-    mu = box_mean(uI, w)
-    pbar = box_mean(up, w)
-    var = box_mean(uI * uI, w) - mu * mu
-    a = (box_mean(uI * up, w) - mu * pbar) / (var + eps)
+    mu = box(uI, w)
+    pbar = box(up, w)
+    var = box(uI * uI, w) - mu * mu
+    a = (box(uI * up, w) - mu * pbar) / (var + eps)
     b = pbar - a * mu
-    return box_mean(a, w) * uI + box_mean(b, w)
+    return box(a, w) * uI + box(b, w)
 
 
 # ---------------------------------------------------------------------------
@@ -205,7 +234,7 @@ def isnr(y, u_orig, u):
 # The algorithm (Sec. 3.1 Steps 0-3, Sec. 3.2)
 # ---------------------------------------------------------------------------
 
-def iterate(H, Y, D2, uE, T, w, eps):
+def iterate(H, Y, D2, uE, T, w, eps, boundary="periodic"):
     """One pass of Steps 1-2: lambda by the discrepancy principle, the two
     deblurring solves, then the guided filter.  Returns a dict with the new
     iterate u and the step's intermediates (lambda, res = ||h*u_E - y||^2,
@@ -213,12 +242,12 @@ def iterate(H, Y, D2, uE, T, w, eps):
     UE = np.fft.fft2(uE)
     lam, res, flag = solve_lambda(H, Y, UE, T)
     uI, up = deblur(H, Y, UE, lam, D2)
-    u = guided_filter(uI, up, w, eps)
+    u = guided_filter(uI, up, w, eps, boundary)
     return {"u": u, "lam": lam, "res": res, "flag": flag, "uI": uI, "up": up}
 
 
 def solve(y, h, sigma, w, eps, iters, u_orig=None, u_init=None, rho=None,
-          trace=False):
+          trace=False, boundary="periodic"):
     """The whole method (Sec. 3.1 Steps 0-3 with Sec. 3.2's lambda).
 
     Step 0 sets u_E = 0 (or ``u_init``, for resuming).  Each iteration k runs
@@ -240,7 +269,7 @@ def solve(y, h, sigma, w, eps, iters, u_orig=None, u_init=None, rho=None,
     if trace:
         out.update({"uE": [], "uI": [], "up": [], "u_k": []})
     for _ in range(iters):
-        st = iterate(H, Y, D2, uE, T, w, eps)
+        st = iterate(H, Y, D2, uE, T, w, eps, boundary)
         out["lam"].append(st["lam"])
         out["res"].append(st["res"])
         out["flag"].append(st["flag"])

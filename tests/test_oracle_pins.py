@@ -380,6 +380,79 @@ def test_guided_filter_invariants():
 
 
 # ---------------------------------------------------------------------------
+# Guided filter with windows truncated at the canvas edge (He et al.'s box
+# filter, cited in Sec. 3.1): every mean over the window's in-canvas pixels
+# ---------------------------------------------------------------------------
+
+def gf_bruteforce_truncated(I, p, w, eps):
+    """Per-pixel loops over the in-canvas part of every window, Eq. 3-5
+    written out with the pixel count of each window as its normaliser."""
+    M, N = I.shape
+    r = (w - 1) // 2
+
+    def window(A, i, j):
+        return np.array([A[y, x] for y in range(max(0, i - r), min(M, i + r + 1))
+                         for x in range(max(0, j - r), min(N, j + r + 1))])
+
+    a = np.zeros((M, N))
+    b = np.zeros((M, N))
+    for i in range(M):
+        for j in range(N):
+            Iv, pv = window(I, i, j), window(p, i, j)
+            mu, pb = Iv.mean(), pv.mean()
+            a[i, j] = (np.mean(Iv * pv) - mu * pb) / (np.mean((Iv - mu) ** 2) + eps)
+            b[i, j] = pb - a[i, j] * mu
+    u = np.zeros((M, N))
+    for i in range(M):
+        for j in range(N):
+            u[i, j] = window(a, i, j).mean() * I[i, j] + window(b, i, j).mean()
+    return u
+
+
+def test_box_mean_truncated_matches_window_loops():
+    x = RNG.random((6, 10))
+    for w in (1, 3, 5, 9, 13):
+        r = (w - 1) // 2
+        ref = np.zeros_like(x)
+        for i in range(6):
+            for j in range(10):
+                ref[i, j] = x[max(0, i - r):i + r + 1, max(0, j - r):j + r + 1].mean()
+        assert np.abs(O.box_mean_truncated(x, w) - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("shape,w", [((7, 9), 3), ((7, 9), 5), ((5, 6), 7), ((12, 8), 9)])
+def test_guided_filter_truncated_matches_bruteforce(shape, w):
+    I = RNG.random(shape)
+    p = I + 0.1 * RNG.standard_normal(shape)
+    got = O.guided_filter(I, p, w, 1e-3, boundary="truncated")
+    assert np.abs(got - gf_bruteforce_truncated(I, p, w, 1e-3)).max() < 1e-12
+
+
+def test_guided_filter_truncated_special_cases():
+    I = RNG.random((11, 13))
+    p = RNG.random((11, 13))
+    eps = 1e-3
+    # constant image is a fixed point; w = 1 returns p
+    c = np.full((11, 13), 0.6)
+    assert np.abs(O.guided_filter(c, c, 5, eps, "truncated") - 0.6).max() < 1e-14
+    assert np.abs(O.guided_filter(I, p, 1, eps, "truncated") - p).max() < 1e-14
+    # a window reaching past every edge holds the whole canvas everywhere:
+    # one global linear regression of p on I (closed form)
+    w = 2 * 13 + 1
+    a = (np.mean(I * p) - I.mean() * p.mean()) / (np.var(I) + eps)
+    b = p.mean() - a * I.mean()
+    assert np.abs(O.guided_filter(I, p, w, eps, "truncated") - (a * I + b)).max() < 1e-12
+    # pixels at least 2r from every edge see only in-canvas windows: there the
+    # truncated and periodic filters agree
+    w, r = 3, 1
+    t = O.guided_filter(I, p, w, eps, "truncated")
+    g = O.guided_filter(I, p, w, eps, "periodic")
+    assert np.abs(t[2 * r:-2 * r, 2 * r:-2 * r] - g[2 * r:-2 * r, 2 * r:-2 * r]).max() < 1e-13
+    # and they differ next to the edge (the windows there wrap or are cut)
+    assert np.abs(t[0] - g[0]).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
 # ISNR (Sec. 4) and the whole iteration
 # ---------------------------------------------------------------------------
 
