@@ -39,6 +39,8 @@ WORKLOAD = "batched_256_uneven_{256,384->512,512,1024x768->1024}_15it"
 PHASE_BYTES = {"row_fwd": 8, "col_fwd_lambda": 16, "lambda_pass": 12, "col_solve_inv": 20,
                "row_inv": 16, "guided_filter": 12, "guided_filter_isnr": 16}
 B_ALG = 68  # bytes per pixel-iteration of the whole iteration (one-pass transforms)
+C4_BATCH, C4_ITERS = 4, 30
+C4_WORKLOAD = "large_4x4096^2_motion31_w9_eps1e-4_30it"
 
 
 # ---------------------------------------------------------------------------
@@ -104,6 +106,16 @@ def generate(indices, workers=None):
         return [_gen(i) for i in indices]
     with mp.get_context("spawn").Pool(workers) as pool:
         return pool.map(_gen, indices, chunksize=4)
+
+
+def _gen_c4(j):
+    import synthetic
+    return synthetic.config_c4_image(j, iters=C4_ITERS)
+
+
+def _gen_table1(t):
+    import synthetic
+    return synthetic.config_table1(t)
 
 
 def load_peaks():
@@ -173,6 +185,20 @@ class ClockSampler:
 # the oracle (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
 
+def host_cpu():
+    """Host CPU of this machine: logical CPUs (nproc) and the lscpu model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        model = None
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def oracle_sample(probs, budget_s=None):
     """Time the FP64 oracle, as it stands, over whole problems (all
     iterations); returns (Mpx-iter/s, seconds, true px-iters, results)."""
@@ -225,6 +251,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "images": N_IMAGES, "iters": ITERS},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "host": host_cpu(),
                          "sample": "one whole image per step, cycling one image of each "
                                    f"size class ({len(probs)} classes), {ITERS} iterations"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -236,6 +263,92 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+
+def roofline_of(phases, canvas_px, iters, hbm_peak):
+    """Dominant iteration phase of an event-timed solve and its achieved
+    algorithmic GB/s (bytes per launch / average launch duration)."""
+    iter_phases = [k for k in phases if k not in ("setup", "copy")]
+    dom = max(iter_phases, key=lambda k: phases[k])
+    per_px = PHASE_BYTES["guided_filter_isnr" if dom == "guided_filter" else dom]
+    achieved = per_px * canvas_px * iters / (phases[dom] / 1e3) / 1e9
+    return dom, per_px, achieved, achieved / hbm_peak
+
+
+def run_large_leg(args, gfd, torch, dev, stream, var_mode, hbm_peak):
+    """The large-image bandwidth-stress workload: 4 images of 4096 x 4096,
+    31 x 31 motion blur, w = 9, eps = 1e-4, 30 iterations, one batched solve
+    per step (graph replay), inputs resident in HBM (0.4 GB per image of
+    workspace and planes, far above L2)."""
+    with mp.get_context("spawn").Pool(C4_BATCH) as pool:
+        probs = pool.map(_gen_c4, range(C4_BATCH))
+    items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
+              "sigma": p.sigma, "w": p.w, "eps": p.eps,
+              "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
+    ctx = gfd.Context(dev.index or 0, var_precision=var_mode)
+    arr = ctx.make_images(items, C4_ITERS)
+    for _ in range(2):
+        ctx.solve_batched_images(arr, C4_ITERS, stream)
+    torch.cuda.synchronize(dev)
+    st = ctx.status(len(items))
+    steps = max(1, min(args.steps, 5))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.solve_batched_images(arr, C4_ITERS, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    px = sum(p.shape[0] * p.shape[1] for p in probs)
+    value = px * C4_ITERS / (ms / 1e3) / 1e6
+    phase_ms, _ = ctx.solve_batched_timed(arr, C4_ITERS, stream)
+    phases = dict(zip(gfd.PHASES, phase_ms))
+    dom, per_px, achieved, frac = roofline_of(phases, px, C4_ITERS, hbm_peak)
+    ctx.close()
+    return {"workload": C4_WORKLOAD, "value": value, "unit": UNIT, "ms_per_solve": ms,
+            "steps": steps, "hbm_frac_alg": B_ALG * value * 1e6 / (hbm_peak * 1e9),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": frac,
+                         "algorithmic_bytes": f"{per_px} B per px per launch"},
+            "phase_ms_per_solve": {k: round(v, 3) for k, v in phases.items()},
+            "status_nonzero": sum(1 for s_ in st if s_ & ~gfd.STATUS_NONCONVERGED)}
+
+
+def run_table1(args):
+    """The paper's five Table 1 settings on synthetic 256^2 stand-ins, solved
+    as one batch on the GPU; per setting the lambda and ISNR curves and the
+    oracle's, as one JSON line (the paper's Fig. 3 analogue)."""
+    import numpy as np
+    import torch
+    with mp.get_context("spawn").Pool(5) as pool:
+        probs = pool.map(_gen_table1, range(1, 6))
+        refs = pool.starmap(_oracle_curves, [(p,) for p in probs])
+    import paper_1609_01839_gb300 as gfd
+    dev = torch.device("cuda", 0)
+    items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
+              "sigma": p.sigma, "w": p.w, "eps": p.eps,
+              "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
+    with gfd.Context(0) as ctx:
+        ctx.solve_batched(items, probs[0].iters)
+        torch.cuda.synchronize()
+    out = []
+    for t, p, it, ref in zip(range(1, 6), probs, items, refs):
+        lam, isnr = it["lam"].cpu().numpy(), it["isnr"].cpu().numpy()
+        out.append({"test": t, "psf": p.h.shape, "sigma2_255": round((p.sigma * 255) ** 2, 3),
+                    "lambda": lam.tolist(), "isnr": isnr.tolist(),
+                    "oracle_lambda": ref["lam"], "oracle_isnr": ref["isnr"],
+                    "max_abs_u": float(np.abs(it["u"].cpu().numpy() - ref["u"]).max()),
+                    "max_isnr_err_db": float(np.abs(isnr - np.array(ref["isnr"])).max())})
+    print(json.dumps({"table1_sweep": out, "eps": 7.5e-4, "w": 3, "iters": probs[0].iters,
+                      "image": "synthetic 256x256 rectangles and disks (seed 0)"}), flush=True)
+    return 0
+
+
+def _oracle_curves(p):
+    import oracle
+    r = oracle.solve(p.y, p.h, p.sigma, p.w, p.eps, p.iters, u_orig=p.u_orig)
+    return {"lam": r["lam"], "isnr": r["isnr"], "u": r["u"].astype("float32")}
+
 
 def run_ours(args):
     import numpy as np
@@ -256,7 +369,8 @@ def run_ours(args):
     items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
               "sigma": p.sigma, "w": p.w, "eps": p.eps,
               "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
-    ctx = gfd.Context(local)
+    ctx_var = gfd.VAR_COMPENSATED  # double-float window sums (FP64-equivalent variance)
+    ctx = gfd.Context(local, var_precision=ctx_var)
     arr = ctx.make_images(items, ITERS)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 1)):  # the first call also builds and captures the graph
@@ -300,12 +414,8 @@ def run_ours(args):
     phase_ms, phase_n = ctx.solve_batched_timed(arr, ITERS, stream)
     phases = dict(zip(gfd.PHASES, phase_ms))
     nlaunch = dict(zip(gfd.PHASES, phase_n))
-    iter_phases = [k for k in gfd.PHASES if k not in ("setup", "copy")]
-    dom = max(iter_phases, key=lambda k: phases[k])
-    per_px = PHASE_BYTES["guided_filter_isnr" if dom == "guided_filter" else dom]
-    dom_bytes = per_px * canvas_px * ITERS  # over all launches of the phase in one solve
     hbm_peak, peak_kind = load_peaks()
-    achieved = dom_bytes / (phases[dom] / 1e3) / 1e9
+    dom, per_px, achieved, _ = roofline_of(phases, canvas_px, ITERS, hbm_peak)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
@@ -316,7 +426,7 @@ def run_ours(args):
 
     # plain path: the same images one gfdeconv_solve at a time (direct launches)
     plain_n = min(args.plain_images, len(probs))
-    pctx = gfd.Context(local, use_graphs=False)
+    pctx = gfd.Context(local, use_graphs=False, var_precision=ctx_var)
     for it in items[:2]:
         pctx.solve(it["y"], it["h"], it["sigma"], it["w"], it["eps"], ITERS)
     torch.cuda.synchronize(dev)
@@ -349,6 +459,10 @@ def run_ours(args):
     e2e_step_s = reduce_max(e2e_step_s, dist, dev)
     e2e_value = total_true * ITERS / e2e_step_s / 1e6
 
+    large = None
+    if rank == 0 and not args.no_large:
+        large = run_large_leg(args, gfd, torch, dev, stream, ctx_var, hbm_peak)
+
     # parity spot check + CPU baseline: one image of each size class, oracle FP64
     cpu = None
     parity = None
@@ -359,7 +473,7 @@ def run_ours(args):
         errs = [float(np.abs(items[i]["u"].cpu().numpy() - r["u"]).max()) for i, r in zip(idx, res)]
         isnr_err = [float(np.abs(items[i]["isnr"].cpu().numpy() - np.array(r["isnr"])).max())
                     for i, r in zip(idx, res)]
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{len(sample)} whole images of the batch (one per size class, "
                          f"{ITERS} iterations, {work} true px-iters) in {secs:.1f} s"}
         parity = {"images": idx, "max_abs_u": max(errs), "max_abs_isnr_db": max(isnr_err)}
@@ -370,6 +484,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "images_per_gpu": len(probs), "iters": ITERS,
+                   "var_precision": gfd.VAR_NAMES[ctx_var],
                    "true_px_per_gpu": true_px, "canvas_px_per_gpu": canvas_px,
                    "value_canvas_px": value_canvas,
                    "l2": f"inputs larger than L2: {(canvas_px * 28) / 1e9:.2f} GB resident per solve",
@@ -383,13 +498,14 @@ def run_ours(args):
         "phase_launches_per_solve": nlaunch,
         "plain": {"value": plain_value, "unit": UNIT, "images": plain_n,
                   "batched_over_plain": value / world / plain_value},
-        "cpu_baseline": cpu, "parity_vs_oracle": parity,
+        "cpu_baseline": cpu, "parity_vs_oracle": parity, "large_image": large,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "runs": e2e_reps,
                 "of_runs": "median"},
         "gpu_launches": launches_per_step * args.steps,
         "status_nonzero": sum(1 for s in st if s & ~gfd.STATUS_NONCONVERGED),
         "nonconverged": sum(1 for s in st if s & gfd.STATUS_NONCONVERGED),
+        "passes_exhausted": sum(1 for s in st if s & gfd.STATUS_PASSES_EXHAUSTED),
         "clocks": clocks,
     }
     ctx.close()
@@ -407,13 +523,19 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--plain-images", type=int, default=32)
+    ap.add_argument("--plain-images", type=int, default=N_IMAGES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--images", type=int, default=N_IMAGES,
                     help="images per GPU (the workload is 256; smaller only for profiling)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the batched solves only (for profiler runs)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 4 x 4096^2 bandwidth-stress leg")
+    ap.add_argument("--table1", action="store_true",
+                    help="run the Table 1 settings sweep instead of the benchmark")
     args = ap.parse_args(argv)
+    if args.table1:
+        return run_table1(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

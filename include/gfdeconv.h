@@ -50,17 +50,33 @@ typedef enum {
 } gfd_status;
 
 /* Per-image status bits returned by gfdeconv_status(). */
-#define GFD_STATUS_NONCONVERGED 1 /* Eq. 11 root not found inside [1e-14, inf) */
+#define GFD_STATUS_NONCONVERGED 1 /* Eq. 11 root lies below 1e-14: lambda = 1e-14 returned */
 #define GFD_STATUS_NONFINITE 2    /* a non-finite residual or lambda appeared */
 #define GFD_STATUS_BAD_PSF 4      /* sum of h <= 0 */
 #define GFD_STATUS_BAD_RHO 8      /* Eq. 12 radicand <= 0 */
+#define GFD_STATUS_PASSES_EXHAUSTED 16 /* the lambda pass schedule ran out with the
+                                          root still bracketed: lambda is the
+                                          bracket's geometric midpoint, which may
+                                          miss the requested lambda_rtol */
+
+/* Arithmetic of the guided filter's window statistics (Sec. 2, Eq. 3-4:
+ * mu_k, pbar_k, sigma_k^2 = E[I^2] - mu_k^2 and the covariance are formed from
+ * window sums of I, p, I^2 and I p).  Every variant takes the statistics about
+ * a per-strip reference value (a_k and b_k do not depend on it). */
+#define GFD_VAR_COMPENSATED 0  /* double-float (FP32 pairs, error-free two-sum and
+                                  two-product) running sums: ~48-bit sums (default) */
+#define GFD_VAR_FP64 1         /* FP64 accumulators (reference point; slow on this part) */
+#define GFD_VAR_FP32 2         /* plain FP32 sums about the reference (precision study) */
+#define GFD_VAR_FP32_RAW 3     /* plain FP32 sums of the raw values, no reference shift */
+
+/* Window boundary of the guided filter (Sec. 2). */
+#define GFD_BOUNDARY_PERIODIC 0  /* windows wrap around the canvas; every window holds
+                                    w^2 pixels and Eq. 3 and 5's 1/w^2 is exact (default) */
+#define GFD_BOUNDARY_TRUNCATED 1 /* windows are cut at the canvas edge and every mean is
+                                    normalised by the number of pixels it covers */
 
 typedef struct {
-  /* Window statistics of the guided filter:
-   * 0 (default) = tile-shifted FP32 sums (the window mean of the guidance is
-   *   taken about a per-tile reference value, which removes the cancellation
-   *   in sigma_k^2 = E[I^2] - mu^2 for locally smooth content);
-   * 1 = plain FP32 sums (for the precision study). */
+  /* Window-statistics arithmetic: one of GFD_VAR_* (0 = compensated). */
   int var_precision;
   /* rho of the discrepancy target (Sec. 3.2): <= 0 selects Eq. 12, else a
    * fixed value in (0, 1]. */
@@ -68,6 +84,19 @@ typedef struct {
   /* 1 (default): capture each solve as a CUDA graph and replay it when the
    * same batch (pointers, sizes, parameters) is solved again. */
   int use_graphs;
+  /* Spectral passes of Eq. 11 launched per iteration after the one fused
+   * into the forward transform (images whose root is resolved skip them);
+   * <= 0 selects 4, at most 16.  If an image's root is still bracketed after
+   * the last one, GFD_STATUS_PASSES_EXHAUSTED is set. */
+  int lambda_max_passes;
+  /* Relative width of the final lambda bracket (the root search stops below
+   * it); <= 0 selects 1e-13, else in [1e-14, 1e-2]. */
+  double lambda_rtol;
+  /* Guided-filter window boundary: one of GFD_BOUNDARY_* (0 = periodic). */
+  int boundary;
+  /* Path of a tile-shape file written by gfdeconv_autotune (read at create;
+   * NULL or "" = built-in shapes).  The string is not retained. */
+  const char* tune_cache;
 } gfdeconv_opts;
 
 /* One image of a batched solve.  All pointers are device pointers. */
@@ -145,8 +174,11 @@ int gfdeconv_fft2_r2c(gfdeconv_ctx* ctx, const float* x, int M, int N, float* X,
  *
  * Limit: M*N <= GFD_NOALLOC_MAX_PIXELS (1024 x 1024); larger sizes return
  * GFD_ERR_SCRATCH_LIMIT before any work.  The first call on each device looks
- * up the scratch address with cudaGetSymbolAddress and caches it: make that
- * first call outside any stream capture.  Nothing in the scratch has to start
+ * up the scratch address with cudaGetSymbolAddress and caches it for the
+ * process (host threads may race on that first call safely): make that first
+ * call outside any stream capture.  The cached address belongs to the
+ * device's current context; after cudaDeviceReset on that device, create a
+ * new gfdeconv context and do not use this entry point again in the process.  Nothing in the scratch has to start
  * at zero: every call writes the descriptor and the whole intermediate plane
  * before reading them.  The scratch is shared by every call on a device, so
  * calls whose stream work overlaps (different streams, or different host
@@ -192,6 +224,14 @@ long long gfdeconv_last_launch_count(gfdeconv_ctx* ctx);
 /* Text of the last CUDA runtime error behind a GFD_ERR_CUDA / GFD_ERR_ALLOC
  * return on this host thread ("no error" if none; static storage). */
 const char* gfdeconv_last_cuda_error(void);
+
+/* Architecture check: *binary_version receives the compute capability the
+ * library's device code was compiled for, as the CUDA runtime reports it for
+ * one library kernel loaded on `cuda_device` (cudaFuncAttributes::binaryVersion,
+ * major * 10 + minor: 103 for sm_103a), and *device_cc the device's own
+ * compute capability in the same form.  Either pointer may be NULL.  Needs a
+ * CUDA device: without one it returns GFD_ERR_CUDA and writes nothing. */
+int gfdeconv_device_arch(int cuda_device, int* binary_version, int* device_cc);
 
 /* Human-readable text for a gfd_status code (static storage). */
 const char* gfdeconv_strerror(int code);

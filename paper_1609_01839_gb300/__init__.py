@@ -16,6 +16,8 @@ import re
 __all__ = [
     "Context", "GfdError", "lib", "library_path", "header_functions",
     "STATUS_NONCONVERGED", "STATUS_NONFINITE", "STATUS_BAD_PSF", "STATUS_BAD_RHO",
+    "STATUS_PASSES_EXHAUSTED", "VAR_COMPENSATED", "VAR_FP64", "VAR_FP32", "VAR_FP32_RAW",
+    "BOUNDARY_PERIODIC", "BOUNDARY_TRUNCATED",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -27,6 +29,17 @@ STATUS_NONCONVERGED = 1
 STATUS_NONFINITE = 2
 STATUS_BAD_PSF = 4
 STATUS_BAD_RHO = 8
+STATUS_PASSES_EXHAUSTED = 16
+# window-statistics arithmetic of the guided filter (gfdeconv_opts.var_precision)
+VAR_COMPENSATED = 0
+VAR_FP64 = 1
+VAR_FP32 = 2
+VAR_FP32_RAW = 3
+VAR_NAMES = {VAR_COMPENSATED: "compensated", VAR_FP64: "fp64", VAR_FP32: "fp32_shifted",
+             VAR_FP32_RAW: "fp32_raw"}
+# guided-filter window boundary (gfdeconv_opts.boundary)
+BOUNDARY_PERIODIC = 0
+BOUNDARY_TRUNCATED = 1
 ERR_SCRATCH_LIMIT = -8  # gfdeconv_fft2_r2c_noalloc: M*N above its static scratch
 NUM_PHASES = 8
 PHASES = ("setup", "row_fwd", "col_fwd_lambda", "lambda_pass", "col_solve_inv", "row_inv",
@@ -65,7 +78,9 @@ class Image(ctypes.Structure):
 class Opts(ctypes.Structure):
     """Mirror of gfdeconv_opts."""
     _fields_ = [("var_precision", ctypes.c_int), ("rho", ctypes.c_double),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("lambda_max_passes", ctypes.c_int),
+                ("lambda_rtol", ctypes.c_double), ("boundary", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 def _load():
@@ -91,6 +106,7 @@ def _load():
         "gfdeconv_last_launch_count": (ctypes.c_longlong, [vp]),
         "gfdeconv_strerror": (ctypes.c_char_p, [ci]),
         "gfdeconv_last_cuda_error": (ctypes.c_char_p, []),
+        "gfdeconv_device_arch": (ci, [ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -101,6 +117,16 @@ def _load():
 
 _lib = _load()
 lib = _lib
+
+
+def device_arch(device: int = 0) -> tuple[int, int]:
+    """(compute capability the library's kernels were built for, as loaded on
+    `device`; the device's compute capability), each major * 10 + minor."""
+    b, d = ctypes.c_int(0), ctypes.c_int(0)
+    rc = _lib.gfdeconv_device_arch(int(device), ctypes.byref(b), ctypes.byref(d))
+    if rc != 0:
+        raise GfdError(rc, "gfdeconv_device_arch")
+    return b.value, d.value
 
 
 def _ptr(t, what, dtype=None, numel=None):
@@ -144,13 +170,16 @@ class Context:
     """A library context on one CUDA device (owns workspaces and cached
     CUDA graphs).  Not thread-safe."""
 
-    def __init__(self, device: int = 0, var_precision: int = 0, rho: float = 0.0,
-                 use_graphs: bool = True):
+    def __init__(self, device: int = 0, var_precision: int = VAR_COMPENSATED, rho: float = 0.0,
+                 use_graphs: bool = True, lambda_max_passes: int = 0, lambda_rtol: float = 0.0,
+                 boundary: int = BOUNDARY_PERIODIC, tune_cache: str | None = None):
         import torch
         torch.cuda.init()
         self.device = device
         self._h = ctypes.c_void_p()
-        opts = Opts(var_precision, rho, 1 if use_graphs else 0)
+        opts = Opts(int(var_precision), float(rho), 1 if use_graphs else 0, int(lambda_max_passes),
+                    float(lambda_rtol), int(boundary),
+                    tune_cache.encode() if tune_cache else None)
         with torch.cuda.device(device):
             rc = _lib.gfdeconv_create(ctypes.byref(self._h), device, ctypes.byref(opts))
         if rc != 0:

@@ -1,6 +1,7 @@
 // C-ABI of the guided-filter deconvolution library: argument validation,
 // workspace and plan management, launch sequencing and CUDA-graph replay.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -285,6 +286,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
       d.sigma = im.sigma;
       d.eps = im.eps;
       d.rho_fixed = c->opts.rho;
+      d.lam_rtol = c->opts.lambda_rtol;
       float2** planes[5] = {&d.S, &d.QI, &d.Qp, &d.H, &d.Y};
       for (float2** pp : planes) {
         *pp = reinterpret_cast<float2*>(cur);
@@ -356,7 +358,8 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
                    bool chains = false) {
   long long L = 0;
   const Tables t{c->tw, c->d2, c->twdf};
-  const int plain = c->opts.var_precision == 1 ? 1 : 0;
+  const int var_mode = c->opts.var_precision, boundary = c->opts.boundary;
+  const int passes = c->opts.lambda_max_passes;
   const HostCopies* hc = pl.copies;
   auto issue = [&](const std::vector<HostCopy>& v, cudaStream_t q) -> cudaError_t {
     for (const HostCopy& cp : v) GFD_CK(cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cp.kind, q));
@@ -404,16 +407,16 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
         GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
         L += 2;
       }
-      for (int p = 1; p <= LAMBDA_FALLBACK_PASSES; ++p)
+      for (int p = 1; p <= passes; ++p)
         for (auto& cl : classes) {
-          GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == LAMBDA_FALLBACK_PASSES, s));
+          GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == passes, s));
           ++L;
         }
       for (auto& cl : classes) {
         GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
         GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
                                                 1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
-        GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, plain, s));
+        GFD_T(GFD_PHASE_GUIDED_FILTER, launch_guided_filter(cl, k, var_mode, boundary, s));
         L += 2 + cl.n_rad_groups;  // one guided-filter launch per window radius
       }
     }
@@ -586,7 +589,18 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return map_err(e);
   if (cuda_device < 0 || cuda_device >= ndev) return GFD_ERR_INVALID_ARG;
-  if (opts && (opts->rho > 1.0 || !std::isfinite(opts->rho))) return GFD_ERR_INVALID_ARG;
+  if (opts) {
+    if (opts->rho > 1.0 || !std::isfinite(opts->rho)) return GFD_ERR_INVALID_ARG;
+    if (opts->var_precision < GFD_VAR_COMPENSATED || opts->var_precision > GFD_VAR_FP32_RAW)
+      return GFD_ERR_INVALID_ARG;
+    if (opts->boundary != GFD_BOUNDARY_PERIODIC && opts->boundary != GFD_BOUNDARY_TRUNCATED)
+      return GFD_ERR_INVALID_ARG;
+    if (opts->lambda_max_passes > 16) return GFD_ERR_INVALID_ARG;
+    if (!std::isfinite(opts->lambda_rtol) ||
+        (opts->lambda_rtol > 0.0 && (opts->lambda_rtol < 1e-14 || opts->lambda_rtol > 1e-2)))
+      return GFD_ERR_INVALID_ARG;
+    if (opts->tune_cache && opts->tune_cache[0]) return GFD_ERR_INVALID_ARG;
+  }
   if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return map_err(e);
   gfdeconv_ctx* c = new (std::nothrow) gfdeconv_ctx();
   if (!c) return GFD_ERR_ALLOC;
@@ -594,10 +608,14 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   if (opts) {
     c->opts = *opts;
   } else {
-    c->opts.var_precision = 0;
+    c->opts.var_precision = GFD_VAR_COMPENSATED;
     c->opts.rho = 0.0;
     c->opts.use_graphs = 1;
+    c->opts.boundary = GFD_BOUNDARY_PERIODIC;
   }
+  if (c->opts.lambda_max_passes <= 0) c->opts.lambda_max_passes = LAMBDA_FALLBACK_PASSES;
+  if (c->opts.lambda_rtol <= 0.0) c->opts.lambda_rtol = 1e-13;
+  c->opts.tune_cache = nullptr;  // not retained
   e = configure_kernels();
   if (e != cudaSuccess) {
     delete c;
@@ -980,7 +998,7 @@ int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, 
   cl.max_rad = (w - 1) / 2;
   cl.n_rad_groups = 1;
   cl.rad_groups[0] = RadGroup{0, 1, (w - 1) / 2};
-  if ((e = launch_guided_filter(cl, -1, c->opts.var_precision == 1 ? 1 : 0, s)) != cudaSuccess)
+  if ((e = launch_guided_filter(cl, -1, c->opts.var_precision, c->opts.boundary, s)) != cudaSuccess)
     return map_err(e);
   return map_err(aux_finish(a, s));
 }
@@ -1074,7 +1092,10 @@ static_assert(sizeof(ImgDesc) <= 256, "descriptor slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GFD_NOALLOC_SCRATCH_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+// Device address of g_noalloc_scratch per device (null until looked up).
+// Atomic: host threads making their first call on a device at the same time
+// both look the address up and store the same value.
+std::atomic<void*> g_noalloc_addr[NOALLOC_MAX_DEVICES];
 
 __global__ void k_store_desc(ImgDesc d, ImgDesc* dst) { *dst = d; }
 
@@ -1091,12 +1112,12 @@ int gfdeconv_fft2_r2c_noalloc(gfdeconv_ctx* c, const float* x, int M, int N, flo
   if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES) return GFD_ERR_INVALID_ARG;
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
   cudaError_t e;
-  if (!g_noalloc_addr[c->device]) {
-    void* p = nullptr;
-    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return map_err(e);
-    g_noalloc_addr[c->device] = p;
+  void* addr = g_noalloc_addr[c->device].load(std::memory_order_acquire);
+  if (!addr) {
+    if ((e = cudaGetSymbolAddress(&addr, g_noalloc_scratch)) != cudaSuccess) return map_err(e);
+    g_noalloc_addr[c->device].store(addr, std::memory_order_release);
   }
-  char* base = static_cast<char*>(g_noalloc_addr[c->device]);
+  char* base = static_cast<char*>(addr);
   cudaStream_t s = (cudaStream_t)stream;
   ImgDesc d{};
   d.u = const_cast<float*>(x);
@@ -1112,5 +1133,22 @@ int gfdeconv_fft2_r2c_noalloc(gfdeconv_ctx* c, const float* x, int M, int N, flo
   const Tables t{c->tw, c->d2, c->twdf};
   if ((e = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s)) != cudaSuccess) return map_err(e);
   if ((e = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s)) != cudaSuccess) return map_err(e);
+  return GFD_OK;
+}
+
+int gfdeconv_device_arch(int cuda_device, int* binary_version, int* device_cc) {
+  using namespace gfd;
+  cudaError_t e = cudaSetDevice(cuda_device);
+  if (e != cudaSuccess) return map_err(e);
+  cudaFuncAttributes a{};
+  if ((e = cudaFuncGetAttributes(&a, (const void*)k_store_desc)) != cudaSuccess) return map_err(e);
+  int major = 0, minor = 0;
+  if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, cuda_device)) !=
+          cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, cuda_device)) !=
+          cudaSuccess)
+    return map_err(e);
+  if (binary_version) *binary_version = a.binaryVersion;
+  if (device_cc) *device_cc = major * 10 + minor;
   return GFD_OK;
 }

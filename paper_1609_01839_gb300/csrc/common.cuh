@@ -24,7 +24,7 @@ GFD_HD int tab_off(int L) { return L - 2; }
 // Number of interpolation nodes for the regularisation-parameter equation
 // (Sec. 3.2, Eq. 11) evaluated per spectral pass.
 constexpr int KNODES = 12;
-// Fallback passes launched after the fused pass of each iteration.
+// Fallback passes launched after the fused pass of each iteration (default).
 constexpr int LAMBDA_FALLBACK_PASSES = 4;
 constexpr double LAMBDA_LO = 1e-14;
 
@@ -33,6 +33,7 @@ constexpr int ST_NONCONVERGED = 1;
 constexpr int ST_NONFINITE = 2;
 constexpr int ST_BAD_PSF = 4;
 constexpr int ST_BAD_RHO = 8;
+constexpr int ST_PASSES_EXHAUSTED = 16;
 
 GFD_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 GFD_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -111,6 +112,7 @@ struct ImgState {
   int status;        // ST_* bits
   int iter;          // iteration index of the pending outputs
   int pad_;
+  double rtol;       // relative width of lambda at which the root search stops
 };
 
 // Per-image parameters and pointers, device memory.
@@ -125,6 +127,7 @@ struct ImgDesc {
   double* res_out;    // [iters] or null
   int kh, kw, w, pad_;
   double sigma, eps, rho_fixed;
+  double lam_rtol;    // relative width of lambda at which the root search stops
   // workspace planes (M*N/2 complex each)
   // spectra are packed half spectra in the class's column-tiled layout
   float2* S;          // forward spectrum scratch (row pass output, then U_E)

@@ -1,5 +1,6 @@
-// Guided filter u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5) with
-// periodic windows, r = (w-1)/2.
+// Guided filter u = guidfilter(u_I, u_p, w, eps) (Sec. 2, Eq. 3-5), r = (w-1)/2,
+// with periodic windows (every window holds w^2 pixels) or windows truncated
+// at the canvas edge (every mean divided by the number of pixels it covers).
 //
 // Every warp works alone, down a strip of GFW_COLS input columns (4 per
 // lane): no block barriers.  Input rows enter a per-warp ring in shared
@@ -7,29 +8,37 @@
 // copies and reads only its own 4 columns.  For the item's rows the warp
 // forms, row by row,
 //   1. window sums down its columns of J = I - c_I, Q = p - c_p, J^2, J Q
-//      (in registers; re-formed directly every GFW_SUB rows and slid in
-//      between, so no sum is carried over more than GFW_SUB - 1 slides),
+//      (in registers; slid from row to row, and for plain FP32 sums re-formed
+//      directly every 4 rows),
 //   2. window sums along the row by warp shuffles (the 2r neighbouring
 //      columns come from the adjacent lanes) -> mu_k, pbar_k, sigma_k^2 and
 //      the covariance -> a_k (Eq. 3), b_k (Eq. 4) for each column,
 //   3. window sums of a and b down the columns (a per-warp ring of the last
 //      2r+1 rows of a, b in shared memory, each lane touching only its own
-//      columns), re-formed / slid like 1.,
+//      columns), re-formed every 4 rows and slid in between,
 //   4. window sums along the row by shuffles -> abar, bbar ->
 //      u = abar I + bbar (Eq. 5), stored as 16-byte vectors.
 // The strip's outer 4*ceil(r/2) columns on each side are halo (their sums
 // are incomplete); the columns in between are the item's output, so
 // neighbouring strips overlap by the halo.  Input rows and columns wrap
-// periodically.  Window statistics are taken about reference values (c_I,
-// c_p: the item's centre pixel), which removes the cancellation in
-// sigma_k^2 = E[I^2] - mu^2 where the window mean is close to c_I.
+// periodically (truncated windows mask the wrapped ones to zero).  Window
+// statistics are taken about reference values (c_I, c_p: the item's centre
+// pixel): a_k and b_k do not depend on them, and the sums of J^2 and J Q are
+// smaller about a nearby reference.
+//
+// The arithmetic of the window sums of step 1-2 is a policy (GFD_VAR_*):
+// double-float running sums (every addition and product error-free), FP64
+// accumulators, or plain FP32.  sigma_k^2 and the covariance are then formed
+// as (n S_JJ - S_J^2) / n^2 and (n S_JQ - S_J S_Q) / n^2 in that arithmetic
+// and rounded to FP32 once.
 #include "common.cuh"
+#include "df.cuh"
 #include "launch.h"
 
 namespace gfd {
 
 constexpr int GFW_COLS = 128;   // input columns per strip (4 per lane)
-constexpr int GFW_SUB = 4;      // rows between direct re-formations of the column sums
+constexpr int GFW_SUB = 4;      // rows between direct re-formations of FP32 column sums
 constexpr int GFW_WARPS = 4;    // warps per block
 constexpr int GFW_AHEAD = 2;    // input rows requested ahead of use
 constexpr int GF_RMAX = 8;      // w <= 17
@@ -49,29 +58,77 @@ GFD_HD int gfw_ring_floats(int rad) {
 }
 static int gfw_wout(int rad) { return GFW_COLS - 8 * ((rad + 1) / 2); }
 
-// Window sums of radius RAD along the strip: v[k] is column 4*lane + k;
-// s[k] = sum of columns 4*lane + k - RAD .. 4*lane + k + RAD.  Columns beyond
-// the warp's edges are not available: the lanes within RAD columns of an
-// edge get incomplete sums (those columns are halo).
-template <int RAD>
-GFD_D void hsum4(const float (&v)[4], float (&s)[4]) {
-  constexpr int E = 2 * RAD + 4;
-  float e[E];  // columns 4*lane - RAD .. 4*lane + 3 + RAD
+// ---------------------------------------------------------------------------
+// Window-sum arithmetic (one policy per GFD_VAR_* mode).  kSub: rows between
+// direct re-formations of the column sums (the exact policies only slide).
+// ---------------------------------------------------------------------------
+struct SumF32 {
+  static constexpr int kSub = GFW_SUB;
+  float v;
+  GFD_D void clear() { v = 0.0f; }
+  GFD_D void add(float x) { v += x; }
+  GFD_D void add_prod(float x, float y) { v = fmaf(x, y, v); }
+};
+
+struct SumF64 {
+  static constexpr int kSub = 1 << 30;
+  double v;
+  GFD_D void clear() { v = 0.0; }
+  GFD_D void add(float x) { v += (double)x; }
+  GFD_D void add_prod(float x, float y) { v = fma((double)x, (double)y, v); }  // exact product
+};
+
+// hi: the FP32-rounded running sum; lo: the exact rounding errors of every
+// addition (two-sum) and product (two-product), summed in FP32.
+struct SumDF {
+  static constexpr int kSub = 1 << 30;
+  float hi, lo;
+  GFD_D void clear() { hi = lo = 0.0f; }
+  GFD_D void add(float x) {
+    const df t = two_sum(hi, x);
+    hi = t.hi;
+    lo += t.lo;
+  }
+  GFD_D void add_prod(float x, float y) {
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);
+    const df t = two_sum(hi, p);
+    hi = t.hi;
+    lo += t.lo + e;
+  }
+};
+
+// Value of lane (lane + off) (compile-time offset after unrolling).
+template <class T>
+GFD_D T lane_shift(T v, int off) {
+  if (off > 0) return __shfl_down_sync(FULL, v, off);
+  if (off < 0) return __shfl_up_sync(FULL, v, -off);
+  return v;
+}
+
+// e[q] = the value of strip column 4*lane + q - RAD, q < 2 RAD + 4, gathered
+// from v[k] = column 4*lane + k of every lane.  Columns beyond the warp's
+// edges are not available: lanes within RAD columns of an edge get values
+// of other columns (those lanes' sums are halo and never used).
+template <int RAD, class T>
+GFD_D void gather_row(const T (&v)[4], T (&e)[2 * RAD + 4]) {
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
+  for (int q = 0; q < 2 * RAD + 4; ++q) {
     const int c = q - RAD;                           // column offset from 4*lane
     const int lo = c >= 0 ? c / 4 : -((3 - c) / 4);  // floor(c / 4): source lane offset
-    const int idx = c - 4 * lo;                      // column within the source lane
-    if (lo == 0)
-      e[q] = v[idx];
-    else if (lo > 0)
-      e[q] = __shfl_down_sync(FULL, v[idx], lo);
-    else
-      e[q] = __shfl_up_sync(FULL, v[idx], -lo);
+    e[q] = lane_shift(v[c - 4 * lo], lo);
   }
-  float acc = 0.0f;
+}
+
+// Window sums of radius RAD along the strip: s[k] = sum of columns
+// 4*lane + k - RAD .. 4*lane + k + RAD.
+template <int RAD, class T>
+GFD_D void hsum4_scalar(const T (&v)[4], T (&s)[4]) {
+  T e[2 * RAD + 4];
+  gather_row<RAD>(v, e);
+  T acc = e[0];
 #pragma unroll
-  for (int q = 0; q <= 2 * RAD; ++q) acc += e[q];
+  for (int q = 1; q <= 2 * RAD; ++q) acc += e[q];
   s[0] = acc;
 #pragma unroll
   for (int k = 1; k < 4; ++k) {
@@ -81,6 +138,104 @@ GFD_D void hsum4(const float (&v)[4], float (&s)[4]) {
 }
 
 template <int RAD>
+GFD_D void hsum4(const float (&v)[4], float (&s)[4]) {
+  hsum4_scalar<RAD>(v, s);
+}
+
+template <int RAD>
+GFD_D void hsum4(const SumF32 (&v)[4], SumF32 (&s)[4]) {
+  const float in[4] = {v[0].v, v[1].v, v[2].v, v[3].v};
+  float out[4];
+  hsum4_scalar<RAD>(in, out);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k].v = out[k];
+}
+
+template <int RAD>
+GFD_D void hsum4(const SumF64 (&v)[4], SumF64 (&s)[4]) {
+  const double in[4] = {v[0].v, v[1].v, v[2].v, v[3].v};
+  double out[4];
+  hsum4_scalar<RAD>(in, out);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k].v = out[k];
+}
+
+// Double-float: the hi parts are added with two-sums (errors kept), the lo
+// parts (already the errors of the column sums) plainly.
+template <int RAD>
+GFD_D void hsum4(const SumDF (&v)[4], SumDF (&s)[4]) {
+  constexpr int E = 2 * RAD + 4;
+  const float vh[4] = {v[0].hi, v[1].hi, v[2].hi, v[3].hi};
+  const float vl[4] = {v[0].lo, v[1].lo, v[2].lo, v[3].lo};
+  float eh[E], el[E];
+  gather_row<RAD>(vh, eh);
+  gather_row<RAD>(vl, el);
+  float hi = eh[0], err = 0.0f, lo = el[0];
+#pragma unroll
+  for (int q = 1; q <= 2 * RAD; ++q) {
+    const df t = two_sum(hi, eh[q]);
+    hi = t.hi;
+    err += t.lo;
+    lo += el[q];
+  }
+  s[0].hi = hi;
+  s[0].lo = err + lo;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    df t = two_sum(hi, eh[k + 2 * RAD]);
+    err += t.lo;
+    t = two_sum(t.hi, -eh[k - 1]);
+    hi = t.hi;
+    err += t.lo;
+    lo += el[k + 2 * RAD] - el[k - 1];
+    s[k].hi = hi;
+    s[k].lo = err + lo;
+  }
+}
+
+// Means and (co)variance of a window of n pixels from S = (sum J, sum Q,
+// sum J^2, sum J Q):  var = (n S_JJ - S_J^2) / n^2 (sigma_k^2, the
+// population variance), cov = (n S_JQ - S_J S_Q) / n^2.
+GFD_D void window_stats(const SumF32& s0, const SumF32& s1, const SumF32& s2, const SumF32& s3,
+                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+  (void)n;
+  mJ = s0.v * inv_n;
+  mQ = s1.v * inv_n;
+  var = fmaf(-mJ, mJ, s2.v * inv_n);
+  cov = fmaf(-mJ, mQ, s3.v * inv_n);
+}
+
+GFD_D void window_stats(const SumF64& s0, const SumF64& s1, const SumF64& s2, const SumF64& s3,
+                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+  (void)inv_n;
+  const double nn = (double)n, inv2 = 1.0 / (nn * nn);
+  mJ = (float)(s0.v / nn);
+  mQ = (float)(s1.v / nn);
+  var = (float)(fma(nn, s2.v, -s0.v * s0.v) * inv2);
+  cov = (float)(fma(nn, s3.v, -s0.v * s1.v) * inv2);
+}
+
+GFD_D void window_stats(const SumDF& s0, const SumDF& s1, const SumDF& s2, const SumDF& s3,
+                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+  const df S0{s0.hi, s0.lo}, S1{s1.hi, s1.lo}, S2{s2.hi, s2.lo}, S3{s3.hi, s3.lo};
+  const df v = df_sub(df_mul_f(S2, n), df_mul(S0, S0));
+  const df c = df_sub(df_mul_f(S3, n), df_mul(S0, S1));
+  const float inv2 = inv_n * inv_n;
+  mJ = (s0.hi + s0.lo) * inv_n;
+  mQ = (s1.hi + s1.lo) * inv_n;
+  var = (v.hi + v.lo) * inv2;
+  cov = (c.hi + c.lo) * inv2;
+}
+
+// Pixels of the window of radius RAD about position x in [0, L) that lie in
+// [0, L) (truncated windows).
+GFD_D int window_count(int x, int L, int RAD) {
+  const int a = x - RAD < 0 ? 0 : x - RAD;
+  const int b = x + RAD > L - 1 ? L - 1 : x + RAD;
+  return b - a + 1;
+}
+
+template <int RAD, class ACC, bool TRUNC>
 GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                      int iter, bool shifted, int H, float* ring, int gwarp, int nwarps) {
   using G = GfwGeom<RAD>;
@@ -90,7 +245,8 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
   const int strips = (N + WOUT - 1) / WOUT;
   const int per_img = strips * (M / H);
   const int n_items = cd.n_img * per_img;
-  const float inv_n = 1.0f / (float)(WIN * WIN);
+  const float n_full = (float)(WIN * WIN);
+  const float inv_full = 1.0f / n_full;
   float* const ra = ring;                   // [WIN][GFW_COLS] a
   float* const rb = ra + WIN * GFW_COLS;    // [WIN][GFW_COLS] b
   float* const rI = rb + WIN * GFW_COLS;    // [RI][GFW_COLS] I
@@ -107,8 +263,21 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
     const float* __restrict__ P = d.up;
     const float* uo = (iter >= 0 && d.isnr_out) ? d.uo : nullptr;
     // this lane's 4 columns (16-byte aligned: x0 and HALO are multiples of 4)
-    const int gx = (x0 - HALO + 4 * lane) & (N - 1);
+    const int xs = x0 - HALO + 4 * lane;  // unwrapped column of the lane's first value
+    const int gx = xs & (N - 1);
     const bool store = out_lane && x0 + 4 * lane - HALO < N;
+    // truncated windows: columns outside the canvas hold zero, and every
+    // window's pixel count along the row
+    float cmask[4] = {1.0f, 1.0f, 1.0f, 1.0f}, ncol[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if constexpr (TRUNC) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = xs + k;
+        const bool in = x >= 0 && x < N;
+        cmask[k] = in ? 1.0f : 0.0f;
+        ncol[k] = in ? (float)window_count(x, N, RAD) : 1.0f;
+      }
+    }
     float cI = 0.0f, cP = 0.0f;
     if (shifted) {
       const size_t c = (size_t)((y0 + H / 2) & (M - 1)) * N + ((x0 + WOUT / 2) & (N - 1));
@@ -128,6 +297,22 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
     auto ring4 = [&](const float* r, int j) {
       return reinterpret_cast<const float4*>(r + (j % RI) * GFW_COLS)[lane];
     };
+    // deviations of input row j about the references (zero outside the
+    // canvas for truncated windows)
+    auto devs = [&](int j, float (&J)[4], float (&Q)[4]) {
+      const float4 iv = ring4(rI, j), pv = ring4(rP, j);
+      J[0] = iv.x - cI; J[1] = iv.y - cI; J[2] = iv.z - cI; J[3] = iv.w - cI;
+      Q[0] = pv.x - cP; Q[1] = pv.y - cP; Q[2] = pv.z - cP; Q[3] = pv.w - cP;
+      if constexpr (TRUNC) {
+        const int yy = y0 - 2 * RAD + j;
+        const float rm = (yy >= 0 && yy < M) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          J[k] *= rm * cmask[k];
+          Q[k] *= rm * cmask[k];
+        }
+      }
+    };
     for (int j = 0; j <= 2 * RAD; ++j) fetch(j);
     cp_async_commit();
 #pragma unroll
@@ -135,7 +320,7 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       fetch(2 * RAD + a);
       cp_async_commit();
     }
-    float V[4][4];   // [J, Q, J^2, J Q][column]: window sums down the columns
+    ACC V[4][4];     // [J, Q, J^2, J Q][column]: window sums down the columns
     float VA[2][4];  // [a, b][column]
     float err = 0.0f;
     // stats row s (image row y0 - r + s) has its column window on input rows
@@ -149,53 +334,69 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       if (uo && store && t >= 0)
         g = __ldg(reinterpret_cast<const float4*>(uo + (size_t)((y0 + t) & (M - 1)) * N + gx));
-      if (s % GFW_SUB == 0) {
+      if (s % ACC::kSub == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int k = 0; k < 4; ++k) V[q][k] = 0.0f;
+          for (int k = 0; k < 4; ++k) V[q][k].clear();
 #pragma unroll
         for (int dd = 0; dd < WIN; ++dd) {
-          const float4 iv = ring4(rI, s + dd), pv = ring4(rP, s + dd);
-          const float J[4] = {iv.x - cI, iv.y - cI, iv.z - cI, iv.w - cI};
-          const float Q[4] = {pv.x - cP, pv.y - cP, pv.z - cP, pv.w - cP};
+          float J[4], Q[4];
+          devs(s + dd, J, Q);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            V[0][k] += J[k];
-            V[1][k] += Q[k];
-            V[2][k] = fmaf(J[k], J[k], V[2][k]);
-            V[3][k] = fmaf(J[k], Q[k], V[3][k]);
+            V[0][k].add(J[k]);
+            V[1][k].add(Q[k]);
+            V[2][k].add_prod(J[k], J[k]);
+            V[3][k].add_prod(J[k], Q[k]);
           }
         }
       } else {
-        const float4 in = ring4(rI, s + 2 * RAD), pn = ring4(rP, s + 2 * RAD);
-        const float4 io = ring4(rI, s - 1), po = ring4(rP, s - 1);
-        const float Jn[4] = {in.x - cI, in.y - cI, in.z - cI, in.w - cI};
-        const float Qn[4] = {pn.x - cP, pn.y - cP, pn.z - cP, pn.w - cP};
-        const float Jo[4] = {io.x - cI, io.y - cI, io.z - cI, io.w - cI};
-        const float Qo[4] = {po.x - cP, po.y - cP, po.z - cP, po.w - cP};
+        float Jn[4], Qn[4], Jo[4], Qo[4];
+        devs(s + 2 * RAD, Jn, Qn);
+        devs(s - 1, Jo, Qo);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          V[0][k] += Jn[k] - Jo[k];
-          V[1][k] += Qn[k] - Qo[k];
-          V[2][k] += fmaf(Jn[k], Jn[k], -Jo[k] * Jo[k]);
-          V[3][k] += fmaf(Jn[k], Qn[k], -Jo[k] * Qo[k]);
+          V[0][k].add(Jn[k]);
+          V[0][k].add(-Jo[k]);
+          V[1][k].add(Qn[k]);
+          V[1][k].add(-Qo[k]);
+          V[2][k].add_prod(Jn[k], Jn[k]);
+          V[2][k].add_prod(-Jo[k], Jo[k]);
+          V[3][k].add_prod(Jn[k], Qn[k]);
+          V[3][k].add_prod(-Jo[k], Qo[k]);
         }
       }
       // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4)
-      float S0[4], S1[4], S2[4], S3[4];
+      ACC S0[4], S1[4], S2[4], S3[4];
       hsum4<RAD>(V[0], S0);
       hsum4<RAD>(V[1], S1);
       hsum4<RAD>(V[2], S2);
       hsum4<RAD>(V[3], S3);
       float A[4], B[4];
+      float nrow = 0.0f, srow_mask = 1.0f;
+      if constexpr (TRUNC) {
+        const int ys = y0 - RAD + s;
+        const bool in = ys >= 0 && ys < M;
+        srow_mask = in ? 1.0f : 0.0f;
+        nrow = in ? (float)window_count(ys, M, RAD) : 1.0f;
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float mJ = S0[k] * inv_n, mQ = S1[k] * inv_n;
-        const float var = fmaf(-mJ, mJ, S2[k] * inv_n);  // sigma_k^2
-        const float cov = fmaf(-mJ, mQ, S3[k] * inv_n);  // mean(I p) - mu pbar
+        float n = n_full, inv_n = inv_full;
+        if constexpr (TRUNC) {
+          n = nrow * ncol[k];
+          inv_n = __frcp_rn(n);
+        }
+        float mJ, mQ, var, cov;
+        window_stats(S0[k], S1[k], S2[k], S3[k], n, inv_n, mJ, mQ, var, cov);
         A[k] = __fdividef(cov, var + eps);  // var + eps >= eps > 0
         B[k] = (mQ + cP) - A[k] * (mJ + cI);
+        if constexpr (TRUNC) {  // windows centred outside the canvas do not exist
+          const float m = srow_mask * cmask[k];
+          A[k] *= m;
+          B[k] *= m;
+        }
       }
       // 3. ring slot s % WIN holds stats row s - WIN until overwritten here
       float4* const sa = reinterpret_cast<float4*>(ra + (s % WIN) * GFW_COLS) + lane;
@@ -239,9 +440,15 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       hsum4<RAD>(VA[1], SB);
       const float4 iv = ring4(rI, s);
       const float ic[4] = {iv.x, iv.y, iv.z, iv.w};
+      float nout = 0.0f;
+      if constexpr (TRUNC) nout = (float)window_count(y0 + t, M, RAD);
       float o[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n);
+      for (int k = 0; k < 4; ++k) {
+        float inv_n = inv_full;
+        if constexpr (TRUNC) inv_n = __frcp_rn(nout * ncol[k]);
+        o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n);
+      }
       if (store) {
         const size_t off = (size_t)((y0 + t) & (M - 1)) * N + gx;
         *reinterpret_cast<float4*>(d.u + off) = make_float4(o[0], o[1], o[2], o[3]);
@@ -274,26 +481,24 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
   }
 }
 
+template <class ACC, bool TRUNC>
 __global__ void __launch_bounds__(GFW_WARPS * 32)
 k_guided_filter(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int iter,
-                int plain_var, int rad, int H) {
+                int shifted_i, int rad, int H) {
   extern __shared__ __align__(16) float gsm[];
   const int warp = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * GFW_WARPS + warp;
   const int nwarps = gridDim.x * GFW_WARPS;
   float* ring = gsm + (size_t)warp * gfw_ring_floats(rad);
-  const bool shifted = plain_var == 0;
+  const bool shifted = shifted_i != 0;
+#define GFD_GF_CASE(R) \
+  case R: gfw_items<R, ACC, TRUNC>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
   switch (rad) {
-    case 0: gfw_items<0>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 1: gfw_items<1>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 2: gfw_items<2>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 3: gfw_items<3>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 4: gfw_items<4>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 5: gfw_items<5>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 6: gfw_items<6>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    case 7: gfw_items<7>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
-    default: gfw_items<8>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
+    GFD_GF_CASE(0) GFD_GF_CASE(1) GFD_GF_CASE(2) GFD_GF_CASE(3) GFD_GF_CASE(4)
+    GFD_GF_CASE(5) GFD_GF_CASE(6) GFD_GF_CASE(7)
+    default: gfw_items<8, ACC, TRUNC>(cd, imgs, st, iter, shifted, H, ring, gwarp, nwarps); break;
   }
+#undef GFD_GF_CASE
 }
 
 static int gf_sm_count() {
@@ -306,11 +511,26 @@ static int gf_sm_count() {
   return n;
 }
 
+using GfKernel = void (*)(ClassDesc, const ImgDesc*, ImgState*, int, int, int, int);
+
+static GfKernel gf_kernel(int var_mode, int boundary) {
+  const bool tr = boundary == GFD_BOUNDARY_TRUNCATED;
+  switch (var_mode) {
+    case GFD_VAR_FP64: return tr ? k_guided_filter<SumF64, true> : k_guided_filter<SumF64, false>;
+    case GFD_VAR_FP32:
+    case GFD_VAR_FP32_RAW: return tr ? k_guided_filter<SumF32, true> : k_guided_filter<SumF32, false>;
+    default: return tr ? k_guided_filter<SumDF, true> : k_guided_filter<SumDF, false>;
+  }
+}
+
 // One launch per window radius present in the class (the images of a class
 // are ordered by radius, so each group is a contiguous range).  Items are
 // (image, strip, block of H rows); H is halved (down to 16) while there are
 // fewer items than resident warps.
-cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, cudaStream_t s) {
+cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int var_mode, int boundary,
+                                 cudaStream_t s) {
+  const GfKernel kern = gf_kernel(var_mode, boundary);
+  const int shifted = var_mode == GFD_VAR_FP32_RAW ? 0 : 1;
   for (int g = 0; g < c.n_rad_groups; ++g) {
     const RadGroup& rg = c.rad_groups[g];
     ClassDesc cd = c.cd;
@@ -318,8 +538,8 @@ cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, 
     cd.n_img = rg.n_img;
     const size_t smem = (size_t)GFW_WARPS * gfw_ring_floats(rg.rad) * sizeof(float);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_guided_filter, GFW_WARPS * 32,
-                                                      smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GFW_WARPS * 32, smem) !=
+            cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
     const int div = c.grid_div > 1 ? c.grid_div : 1;
@@ -331,14 +551,22 @@ cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var, 
     int grid = (per_sm * gf_sm_count() + div - 1) / div;
     const int need = (n_items + GFW_WARPS - 1) / GFW_WARPS;
     if (grid > need) grid = need;
-    k_guided_filter<<<grid, GFW_WARPS * 32, smem, s>>>(cd, c.imgs, c.st, iter, plain_var, rg.rad, H);
+    kern<<<grid, GFW_WARPS * 32, smem, s>>>(cd, c.imgs, c.st, iter, shifted, rg.rad, H);
   }
   return cudaGetLastError();
 }
 
 cudaError_t configure_gf_kernel() {
-  return cudaFuncSetAttribute(k_guided_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(GFW_WARPS * gfw_ring_floats(GF_RMAX) * sizeof(float)));
+  const int bytes = (int)(GFW_WARPS * gfw_ring_floats(GF_RMAX) * sizeof(float));
+  const GfKernel ks[6] = {k_guided_filter<SumDF, false>,  k_guided_filter<SumDF, true>,
+                          k_guided_filter<SumF64, false>, k_guided_filter<SumF64, true>,
+                          k_guided_filter<SumF32, false>, k_guided_filter<SumF32, true>};
+  for (GfKernel k : ks) {
+    const cudaError_t e =
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace gfd

@@ -117,6 +117,7 @@ __global__ void k_setup_init(ClassDesc cd, const ImgDesc* __restrict__ imgs, Img
   S->invT = 1.0 / S->T;
   S->lam = NAN;
   S->need = 0;
+  S->rtol = d.lam_rtol;
   set_bracket(S, INITIAL_LO, INITIAL_HI);
 }
 

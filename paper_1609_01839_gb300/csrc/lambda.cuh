@@ -216,7 +216,7 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
 // bracketed by multisection: every lane evaluates the sign of the
 // interpolant at its own trial point, and the bracket shrinks 33-fold per
 // round.  Returns lambda = exp(t_root).
-GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
+GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) {
   const bool own = lane < KNODES;
   const df tm = own ? df_from_double(log((double)xm)) : df_make(0.0f);
   // All abscissa differences are scaled by a power of two ~ 1/(bracket
@@ -246,7 +246,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
   }
   __syncwarp();
   df a = s_t[j], b = s_t[j + 1];
-  for (int round = 0; round < 8; ++round) {
+  for (int round = 0; round < 10; ++round) {
     // trial point a + (b - a) (lane + 1) / 33
     const df width = df_sub(b, a);
     const df t = df_add(a, df_mul_f(width, (float)(lane + 1) / 33.0f));
@@ -273,7 +273,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, int lane) {
     const df nbv = nb < 32 ? df_add(a, df_mul_f(width, (float)(nb + 1) / 33.0f)) : b;
     a = na;
     b = nbv;
-    if (df_to_double(df_sub(b, a)) <= 1e-13) break;  // absolute in t: relative in lambda
+    if (df_to_double(df_sub(b, a)) <= rtol) break;  // absolute in t: relative in lambda
   }
   return exp(0.5 * (df_to_double(a) + df_to_double(b)));
 }
@@ -374,7 +374,7 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
     int j = 31 - __clz(below | 1u);
     if (j > KNODES - 2) j = KNODES - 2;
     if (mode == MODE_CHEB) {
-      const double lam = interp_root_warp(xm, gm, j, lane);
+      const double lam = interp_root_warp(xm, gm, j, st->rtol, lane);
       resolve_warp(st, lam, iter, lam_out, lane);
       open = false;
     } else {
@@ -384,8 +384,8 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
   }
   if (open) {
     if (lane == 0) st->need = 1;
-    if (last_chance) {
-      if (lane == 0) st->status |= ST_NONCONVERGED;
+    if (last_chance) {  // the pass schedule ran out with the bracket still open
+      if (lane == 0) st->status |= ST_PASSES_EXHAUSTED;
       const double mid = sqrt((double)st->lo * (double)st->hi);
       __syncwarp();
       resolve_warp(st, mid, iter, lam_out, lane);

@@ -71,7 +71,8 @@ cudaError_t launch_lambda_pass(const ClassLaunch& c, int iter, bool last_chance,
 // Spectral solves (Eq. 8, 9) fused with the inverse column FFTs: S -> QI, Qp.
 cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStream_t s);
 // Guided filter (Eq. 3-5): real planes (uI, up) -> u.  iter < 0: no ISNR.
-cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int plain_var,
+// var_mode: GFD_VAR_*; boundary: GFD_BOUNDARY_*.
+cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int var_mode, int boundary,
                                  cudaStream_t s);
 // Double-float 2-D real DFT of real plane src into spectrum plane dst
 // (SEL_H or SEL_YS); uses the S and Q_I planes as scratch.

@@ -26,7 +26,7 @@ __all__ = [
     "psf_uniform", "psf_inv_quadratic", "psf_gaussian", "psf_binomial5",
     "psf_motion", "blur_circular", "sigma_from_bsnr", "mirror_extend",
     "config_c0", "config_c1", "config_c2_image", "config_c2", "config_c4",
-    "config_c4_image", "table1_psf", "next_pow2",
+    "config_c4_image", "config_table1", "table1_psf", "next_pow2",
 ]
 
 
@@ -371,6 +371,22 @@ def config_c4_image(j: int, size: int = 4096, iters: int = 30) -> Problem:
     y, sigma = _degrade(u, h, rng, bsnr_db=35.0)
     return Problem(_f32(y), _f32(h), sigma, 9, 1e-4, iters, _f32(u), (size, size),
                    {"name": f"c4_{j}"})
+
+
+def config_table1(test: int, seed: int = 0, M: int = 256, N: int = 256,
+                  iters: int = 30) -> Problem:
+    """One of the paper's five experiment settings (Sec. 4, Table 1: PSF and
+    noise variance on the [0, 255] scale) on a synthetic 256 x 256 stand-in
+    for its test images (rectangles and disks over a gradient, as in the
+    256^2 workload), with the paper's hand-tuned eps = 7.5e-4 and w = 3
+    (Sec. 4) and about 30 iterations (Sec. 4's timing)."""
+    u = image_rects_disks(seed, M, N)
+    h = table1_psf(test)
+    sigma = math.sqrt(TABLE1_SIGMA2_255[test]) / 255.0
+    rng = np.random.default_rng(seed + 104729 * test)
+    y, sigma = _degrade(u, h, rng, sigma=sigma)
+    return Problem(_f32(y), _f32(h), sigma, 3, 7.5e-4, iters, _f32(u), (M, N),
+                   {"name": f"table1_test{test}", "test": test})
 
 
 def config_c4(batch: int = 4, size: int = 4096, iters: int = 30):

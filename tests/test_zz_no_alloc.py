@@ -56,18 +56,39 @@ def test_two_calls_in_a_row_match_allocating_entry_point(ctx, M, N):
     assert _rel_rms(X3, ref1) <= FFT_RTOL
 
 
+def _free_bytes():
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info(DEV)[0]
+
+
 def test_calls_allocate_no_device_memory(ctx):
+    """On a context that has made no call yet, the first two no-alloc calls
+    leave free device memory unchanged; as a control, the allocating entry
+    point's first call on another fresh context takes its workspace (4 MiB
+    here), which shows that the probe sees an allocation of that size."""
     M, N = 1024, 1024
     x = _image(M, N, 3)
     X = torch.empty((M, N // 2), dtype=torch.complex64, device=DEV)
-    ctx.fft2_r2c_noalloc(x, X)  # first call on the device: symbol lookup
-    torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info(DEV)
-    for _ in range(2):
-        ctx.fft2_r2c_noalloc(x, X)
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info(DEV)
-    assert free1 == free0
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    ctx.fft2_r2c_noalloc(x, X)  # the per-device symbol lookup is done once per process
+    fresh = gfd.Context(0)
+    try:
+        free0 = _free_bytes()
+        for _ in range(2):
+            rc = gfd.lib.gfdeconv_fft2_r2c_noalloc(fresh._h, x.data_ptr(), M, N, X.data_ptr(),
+                                                   stream)
+            assert rc == 0
+        assert _free_bytes() == free0
+    finally:
+        fresh.close()
+    control = gfd.Context(0)
+    try:
+        free0 = _free_bytes()
+        rc = gfd.lib.gfdeconv_fft2_r2c(control._h, x.data_ptr(), M, N, X.data_ptr(), stream)
+        assert rc == 0
+        assert free0 - _free_bytes() >= 4 * M * N
+    finally:
+        control.close()
 
 
 def test_size_beyond_static_scratch_rejected(ctx):
