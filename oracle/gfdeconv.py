@@ -216,6 +216,35 @@ def guided_filter(uI, up, w, eps, boundary="periodic"):
     return box(a, w) * uI + box(b, w)
 
 
+def guided_filter_color(I, p, w, eps, boundary="periodic"):
+    """Guided filter with a colour guidance image (Sec. 3.1 remarks that the
+    guided filter applies to colour as well as grey-scale images): I is
+    M x N x 3, p is M x N.  reading: the local linear model of Eq. 2 with a
+    3-vector slope, u(i) = a_k . I(i) + b_k, whose least-squares solution over
+    window k with the regulariser eps |a_k|^2 of Eq. 3 is
+        a_k = (Sigma_k + eps U)^-1 (mean_k(I p) - mu_k pbar_k)
+        b_k = pbar_k - a_k . mu_k                                  (Eq. 4)
+    with mu_k the window mean of I (3-vector), Sigma_k its window covariance
+    (3 x 3, population), U the identity; the output averages a and b over the
+    windows covering each pixel as in Eq. 5: u = abar . I + bbar.  The 3 x 3
+    systems are solved with numpy.linalg.solve (a library primitive)."""
+    box = BOX_MEANS[boundary]
+    I = np.asarray(I, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    M, N, C = I.shape
+    mu = np.stack([box(I[:, :, c], w) for c in range(C)], axis=-1)
+    pbar = box(p, w)
+    cov_Ip = np.stack([box(I[:, :, c] * p, w) for c in range(C)], axis=-1) - mu * pbar[..., None]
+    Sigma = np.empty((M, N, C, C))
+    for c in range(C):
+        for d in range(C):
+            Sigma[:, :, c, d] = box(I[:, :, c] * I[:, :, d], w) - mu[:, :, c] * mu[:, :, d]
+    a = np.linalg.solve(Sigma + eps * np.eye(C), cov_Ip[..., None])[..., 0]
+    b = pbar - np.sum(a * mu, axis=-1)
+    abar = np.stack([box(a[:, :, c], w) for c in range(C)], axis=-1)
+    return np.sum(abar * I, axis=-1) + box(b, w)
+
+
 # ---------------------------------------------------------------------------
 # Evaluation (Sec. 4)
 # ---------------------------------------------------------------------------

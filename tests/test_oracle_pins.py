@@ -453,6 +453,79 @@ def test_guided_filter_truncated_special_cases():
 
 
 # ---------------------------------------------------------------------------
+# Colour guidance (3-channel I, 3 x 3 window covariance)
+# ---------------------------------------------------------------------------
+
+def gf_color_bruteforce(I, p, w, eps):
+    """Per-pixel loops over periodic windows: the least-squares fit of
+    p ~ a . I + b in each window with penalty eps |a|^2, solved by an explicit
+    3 x 3 Cramer's rule, then the averages of a and b over covering windows."""
+    M, N, C = I.shape
+    r = (w - 1) // 2
+    a = np.zeros((M, N, C))
+    b = np.zeros((M, N))
+    for i in range(M):
+        for j in range(N):
+            X = np.array([I[(i + dy) % M, (j + dx) % N] for dy in range(-r, r + 1)
+                          for dx in range(-r, r + 1)])
+            y = np.array([p[(i + dy) % M, (j + dx) % N] for dy in range(-r, r + 1)
+                          for dx in range(-r, r + 1)])
+            mu, pb = X.mean(axis=0), y.mean()
+            Xc = X - mu
+            A = Xc.T @ Xc / len(y) + eps * np.eye(C)
+            rhs = Xc.T @ (y - pb) / len(y)
+            det = np.linalg.det(A)
+            for c in range(C):
+                Ac = A.copy()
+                Ac[:, c] = rhs
+                a[i, j, c] = np.linalg.det(Ac) / det
+            b[i, j] = pb - a[i, j] @ mu
+    u = np.zeros((M, N))
+    for i in range(M):
+        for j in range(N):
+            sa = np.zeros(C)
+            sb = 0.0
+            for dy in range(-r, r + 1):
+                for dx in range(-r, r + 1):
+                    sa += a[(i + dy) % M, (j + dx) % N]
+                    sb += b[(i + dy) % M, (j + dx) % N]
+            u[i, j] = sa @ I[i, j] / (w * w) + sb / (w * w)
+    return u
+
+
+@pytest.mark.parametrize("shape,w", [((6, 7), 3), ((5, 5), 5), ((8, 6), 1)])
+def test_guided_filter_color_matches_bruteforce(shape, w):
+    I = RNG.random(shape + (3,))
+    p = I.mean(axis=-1) + 0.1 * RNG.standard_normal(shape)
+    got = O.guided_filter_color(I, p, w, 1e-2)
+    assert np.abs(got - gf_color_bruteforce(I, p, w, 1e-2)).max() < 1e-11
+
+
+def test_guided_filter_color_special_cases():
+    I = RNG.random((12, 10, 3))
+    p = RNG.random((12, 10))
+    w, eps = 5, 1e-3
+    g = O.guided_filter_color(I, p, w, eps)
+    # three equal channels: Sigma = var * ones, a = alpha (1, 1, 1) with
+    # (3 var + eps) alpha = cov, i.e. the grey-scale filter with eps / 3
+    G = RNG.random((12, 10))
+    same = O.guided_filter_color(np.stack([G, G, G], axis=-1), p, w, eps)
+    assert np.abs(same - O.guided_filter(G, p, w, eps / 3.0)).max() < 1e-11
+    # constant guidance and input: fixed point; eps -> inf: box(box(p))
+    c = np.full((12, 10), 0.4)
+    assert np.abs(O.guided_filter_color(np.full((12, 10, 3), 0.7), c, w, eps) - 0.4).max() < 1e-13
+    big = O.guided_filter_color(I, p, w, 1e12)
+    assert np.abs(big - O.box_mean(O.box_mean(p, w), w)).max() < 1e-10
+    # affine in p, invariant to a constant added to each guidance channel
+    assert np.abs(O.guided_filter_color(I, 2.0 * p + 0.3, w, eps) - (2.0 * g + 0.3)).max() < 1e-11
+    shift = I + np.array([1.0, -2.0, 0.5])
+    assert np.abs(O.guided_filter_color(shift, p, w, eps) - g).max() < 1e-9
+    # p equal to one guidance channel and eps -> 0: that channel is reproduced
+    ident = O.guided_filter_color(I, I[:, :, 1], w, 1e-13)
+    assert np.abs(ident - I[:, :, 1]).max() < 1e-7
+
+
+# ---------------------------------------------------------------------------
 # ISNR (Sec. 4) and the whole iteration
 # ---------------------------------------------------------------------------
 
