@@ -17,6 +17,6 @@ prints no worked example and its test images are not available.
 from .gfdeconv import (  # noqa: F401
     embed_psf, psf_spectrum, grad_weight, rho_eq12, discrepancy_target,
     residual_norm2, f_lambda, solve_lambda, deblur, box_mean, box_mean_truncated, guided_filter,
-    guided_filter_color,
+    guided_filter_color, pad_symmetric, crop,
     isnr, iterate, solve, NONCONVERGED, LAMBDA_LO, LAMBDA_RTOL,
 )

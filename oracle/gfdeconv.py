@@ -246,6 +246,27 @@ def guided_filter_color(I, p, w, eps, boundary="periodic"):
 
 
 # ---------------------------------------------------------------------------
+# Observation padded to a power-of-two canvas (reading of the paper's silence
+# on image sizes; the variant that pads only y)
+# ---------------------------------------------------------------------------
+
+def pad_symmetric(y, M, N):
+    """y (m x n) extended to M x N by symmetric reflection at its bottom and
+    right edges (the edge sample repeats: ... c b a | a b c ...), so that the
+    circular model of the canvas sees no jump where the canvas wraps.
+    reading: the problem is posed on the true size and only the observation
+    is extended; the solve runs on the canvas and its result is cropped."""
+    y = np.asarray(y, dtype=np.float64)
+    m, n = y.shape
+    return np.pad(y, ((0, M - m), (0, N - n)), mode="symmetric")
+
+
+def crop(u, m, n):
+    """The top-left m x n part of a canvas-sized result."""
+    return np.asarray(u)[:m, :n].copy()
+
+
+# ---------------------------------------------------------------------------
 # Evaluation (Sec. 4)
 # ---------------------------------------------------------------------------
 

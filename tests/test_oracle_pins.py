@@ -526,6 +526,26 @@ def test_guided_filter_color_special_cases():
 
 
 # ---------------------------------------------------------------------------
+# Padding only the observation to the canvas
+# ---------------------------------------------------------------------------
+
+def test_pad_symmetric_matches_index_reflection():
+    y = RNG.random((5, 7))
+    for M, N in ((8, 8), (5, 16), (16, 7), (32, 32)):
+        got = O.pad_symmetric(y, M, N)
+        ref = np.zeros((M, N))
+        for i in range(M):
+            for j in range(N):
+                ti, tj = i % (2 * 5), j % (2 * 7)        # reflection period 2m
+                si = ti if ti < 5 else 2 * 5 - 1 - ti
+                sj = tj if tj < 7 else 2 * 7 - 1 - tj
+                ref[i, j] = y[si, sj]
+        assert np.array_equal(got, ref), (M, N)
+    assert np.array_equal(O.pad_symmetric(y, 5, 7), y)
+    assert np.array_equal(O.crop(O.pad_symmetric(y, 16, 16), 5, 7), y)
+
+
+# ---------------------------------------------------------------------------
 # ISNR (Sec. 4) and the whole iteration
 # ---------------------------------------------------------------------------
 
