@@ -216,6 +216,41 @@ def oracle_sample(probs, budget_s=None):
     return work / dt / 1e6, dt, work, res
 
 
+def _oracle_run(args):
+    """Worker: the oracle on one problem for `iters` iterations; seconds."""
+    p, iters = args
+    import oracle
+    t0 = time.perf_counter()
+    oracle.solve(p.y, p.h, p.sigma, p.w, p.eps, iters, u_orig=p.u_orig)
+    return time.perf_counter() - t0
+
+
+def oracle_detail(cover_probs):
+    """The oracle as it stands, timed on this host: one core on the 256^2
+    (10 iterations) and 512^2 (20) workloads and on 1 of the 30 iterations of
+    one 4096^2 image (its per-iteration rate; the whole 30 would take ~15 min),
+    and all cores (one process per core) over a 16-image subset of the batch
+    that covers every canvas size, PSF and window."""
+    import synthetic
+    out = {}
+    for name, p, iters in (("256x256_10it", synthetic.config_c0(), 10),
+                           ("512x512_20it", synthetic.config_c1(), 20),
+                           ("4096x4096_1of30it", synthetic.config_c4_image(0, iters=1), 1)):
+        secs = _oracle_run((p, iters))
+        px = p.shape[0] * p.shape[1] * iters
+        out[name] = {"Mpx_iter_per_s": px / secs / 1e6, "seconds": round(secs, 2), "cores": 1}
+    n = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(_oracle_run, [(p, p.iters) for p in cover_probs], chunksize=1)
+    secs = time.perf_counter() - t0
+    px = sum(p.true_shape[0] * p.true_shape[1] * p.iters for p in cover_probs)
+    out["batch_subset_all_cores"] = {"Mpx_iter_per_s": px / secs / 1e6, "seconds": round(secs, 2),
+                                     "cores": n, "images": len(cover_probs),
+                                     "note": "measured on the subset (true pixels), not extrapolated"}
+    return out
+
+
 def class_sample(probs):
     """Indices of one image of each canvas/true-size class, in batch order."""
     seen, out = set(), []
@@ -286,6 +321,11 @@ def run_large_leg(args, gfd, torch, dev, stream, var_mode, hbm_peak):
               "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
     ctx = gfd.Context(dev.index or 0, var_precision=var_mode)
     arr = ctx.make_images(items, C4_ITERS)
+    tuned = None
+    if not args.no_tune:
+        ctx.autotune(arr, C4_ITERS, None, stream)
+        col, row, gfr, ch = ctx.tune_get(*probs[0].shape)
+        tuned = {"col_threads": col, "row_threads": row, "gf_rows": gfr, "chains": ch}
     for _ in range(2):
         ctx.solve_batched_images(arr, C4_ITERS, stream)
     torch.cuda.synchronize(dev)
@@ -306,6 +346,7 @@ def run_large_leg(args, gfd, torch, dev, stream, var_mode, hbm_peak):
     dom, per_px, achieved, frac = roofline_of(phases, px, C4_ITERS, hbm_peak)
     ctx.close()
     return {"workload": C4_WORKLOAD, "value": value, "unit": UNIT, "ms_per_solve": ms,
+            "tile_shapes": tuned,
             "steps": steps, "hbm_frac_alg": B_ALG * value * 1e6 / (hbm_peak * 1e9),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": frac,
@@ -373,6 +414,21 @@ def run_ours(args):
     ctx = gfd.Context(local, var_precision=ctx_var)
     arr = ctx.make_images(items, ITERS)
     stream = torch.cuda.current_stream(dev)
+    # tile shapes from the autotuner, measured on this workload (untimed)
+    t0 = time.perf_counter()
+    tune_dir = os.environ.get("GFD_ARTIFACT_DIR", os.path.join(ROOT, "artifacts"))
+    os.makedirs(tune_dir, exist_ok=True)
+    tune_path = os.path.join(tune_dir, f"tune_rank{rank}.txt")
+    if args.no_tune:
+        tuned = None
+    else:
+        ctx.autotune(arr, ITERS, tune_path, stream)
+        tuned = {"seconds": round(time.perf_counter() - t0, 2), "chains": None, "classes": {}}
+        for p in probs:
+            M, N = p.shape
+            col, row, gfr, ch = ctx.tune_get(M, N)
+            tuned["chains"] = ch
+            tuned["classes"][f"{M}x{N}"] = {"col_threads": col, "row_threads": row, "gf_rows": gfr}
     for _ in range(max(args.warmup, 1)):  # the first call also builds and captures the graph
         ctx.solve_batched_images(arr, ITERS, stream)
     torch.cuda.synchronize(dev)
@@ -426,7 +482,8 @@ def run_ours(args):
 
     # plain path: the same images one gfdeconv_solve at a time (direct launches)
     plain_n = min(args.plain_images, len(probs))
-    pctx = gfd.Context(local, use_graphs=False, var_precision=ctx_var)
+    pctx = gfd.Context(local, use_graphs=False, var_precision=ctx_var,
+                       tune_cache=None if args.no_tune else tune_path)
     for it in items[:2]:
         pctx.solve(it["y"], it["h"], it["sigma"], it["w"], it["eps"], ITERS)
     torch.cuda.synchronize(dev)
@@ -473,7 +530,16 @@ def run_ours(args):
         errs = [float(np.abs(items[i]["u"].cpu().numpy() - r["u"]).max()) for i, r in zip(idx, res)]
         isnr_err = [float(np.abs(items[i]["isnr"].cpu().numpy() - np.array(r["isnr"])).max())
                     for i, r in zip(idx, res)]
+        cover = []
+        seen = set()
+        for q in probs:  # first image of each (size, PSF, window) class, up to 16
+            key = (q.shape, q.true_shape, q.meta.get("psf"), q.w)
+            if key not in seen and len(cover) < 16:
+                seen.add(key)
+                cover.append(q)
+        detail = oracle_detail(cover)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+               "detail": detail,
                "sample": f"{len(sample)} whole images of the batch (one per size class, "
                          f"{ITERS} iterations, {work} true px-iters) in {secs:.1f} s"}
         parity = {"images": idx, "max_abs_u": max(errs), "max_abs_isnr_db": max(isnr_err)}
@@ -484,7 +550,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "images_per_gpu": len(probs), "iters": ITERS,
-                   "var_precision": gfd.VAR_NAMES[ctx_var],
+                   "var_precision": gfd.VAR_NAMES[ctx_var], "tile_shapes": tuned,
                    "true_px_per_gpu": true_px, "canvas_px_per_gpu": canvas_px,
                    "value_canvas_px": value_canvas,
                    "l2": f"inputs larger than L2: {(canvas_px * 28) / 1e9:.2f} GB resident per solve",
@@ -529,6 +595,8 @@ def main(argv=None):
                     help="images per GPU (the workload is 256; smaller only for profiling)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the batched solves only (for profiler runs)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the built-in tile shapes instead of the autotuner's")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4 x 4096^2 bandwidth-stress leg")
     ap.add_argument("--table1", action="store_true",

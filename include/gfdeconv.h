@@ -63,11 +63,16 @@ typedef enum {
  * mu_k, pbar_k, sigma_k^2 = E[I^2] - mu_k^2 and the covariance are formed from
  * window sums of I, p, I^2 and I p).  Every variant takes the statistics about
  * a per-strip reference value (a_k and b_k do not depend on it). */
-#define GFD_VAR_COMPENSATED 0  /* double-float (FP32 pairs, error-free two-sum and
-                                  two-product) running sums: ~48-bit sums (default) */
+#define GFD_VAR_COMPENSATED 0  /* split sums (default): each deviation is split on a
+                                  power-of-two grid from a bound on |u_I|, |u_p| into
+                                  an integer leading part (window sums exact in int32,
+                                  n S_II - S_I^2 exact in int64) and an FP32 remainder
+                                  (its sums compensate the leading part's truncation) */
 #define GFD_VAR_FP64 1         /* FP64 accumulators (reference point; slow on this part) */
 #define GFD_VAR_FP32 2         /* plain FP32 sums about the reference (precision study) */
 #define GFD_VAR_FP32_RAW 3     /* plain FP32 sums of the raw values, no reference shift */
+#define GFD_VAR_DOUBLE_FLOAT 4 /* double-float (FP32 pairs, error-free two-sum and
+                                  two-product) running sums: ~48-bit sums */
 
 /* Window boundary of the guided filter (Sec. 2). */
 #define GFD_BOUNDARY_PERIODIC 0  /* windows wrap around the canvas; every window holds
@@ -152,6 +157,29 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* ctx, int n, const gfdeconv_image* 
 int gfdeconv_guidfilter(gfdeconv_ctx* ctx, const float* I, const float* p, int M, int N,
                         int w, double eps, float* u_out, void* stream);
 
+/* Observations whose size is not a power of two (the paper's images are
+ * square powers of two; reading: pad only the observation).  y (m x n,
+ * device) is extended to y_canvas (M x N, device, M >= m, N >= n powers of
+ * two in [8, 4096]) by symmetric reflection at its bottom and right edges
+ * (the edge sample repeated, period 2m and 2n); solve on the canvas, then
+ * gfdeconv_crop takes the top-left m x n part of a canvas result.  Both
+ * return GFD_ERR_INVALID_ARG when m > M or n > N. */
+int gfdeconv_pad_symmetric(gfdeconv_ctx* ctx, const float* y, int m, int n, float* y_canvas,
+                           int M, int N, void* stream);
+int gfdeconv_crop(gfdeconv_ctx* ctx, const float* u_canvas, int M, int N, float* u, int m, int n,
+                  void* stream);
+
+/* Guided filter with a colour guidance image (the guided filter applies to
+ * colour as well as grey-scale images, Sec. 3.1): I is 3 device planes
+ * [3][M][N] (channel-major), p and u_out M*N device planes.  Per window,
+ * a_k = (Sigma_k + eps U)^-1 (mean(I p) - mu_k pbar_k) with Sigma_k the
+ * window covariance of the 3 channels (Eq. 3 with a 3-vector slope),
+ * b_k = pbar_k - a_k . mu_k (Eq. 4), u = abar . I + bbar (Eq. 5).  Window
+ * statistics and the 3 x 3 solves in FP64; periodic or truncated windows as
+ * gfdeconv_opts.boundary selects (var_precision does not apply). */
+int gfdeconv_guidfilter_color(gfdeconv_ctx* ctx, const float* I, const float* p, int M, int N,
+                              int w, double eps, float* u_out, void* stream);
+
 /* 2-D real DFT of x (M*N device) into the packed half spectrum X (device,
  * M*(N/2) complex64 = M*N floats): X[m][l] = F(x)(m, l) for 1 <= l < N/2 and
  * X[m][0] = F(x)(m, 0) + i F(x)(m, N/2).  The DFT diagonalises the circular
@@ -217,6 +245,39 @@ int gfdeconv_status(gfdeconv_ctx* ctx, int* per_image_status, int n);
 int gfdeconv_solve_batched_timed(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
                                  int iters, void* stream, double* phase_ms,
                                  long long* phase_launches);
+
+/* Autotuner of the batched solve (Sec. 3.1's per-iteration steps, scheduled
+ * for this GPU; the paper has no counterpart).  Times the solve of `imgs`
+ * (device buffers, as for gfdeconv_solve_batched; their outputs are
+ * overwritten) on `stream` with event pairs around every launch, for each
+ * candidate of one tile shape at a time:
+ *   col_threads in {64, 128, 256}: threads per column-pass block, which fixes
+ *     the tile width of the spectra (4096-row canvases always use 512);
+ *   row_threads in {64, 128, 256}: threads per row-pass block (rows per item);
+ *   gf_rows in {16, 32, 64}: output rows per guided-filter item;
+ * keeping per canvas size the fastest over the phases the shape affects, then
+ * times graph replays of the solve with 1, 2 and 4 concurrent chains.  The
+ * result applies to the context's later solves and, if `path` is not NULL
+ * or "", is merged into that tile-shape file (other canvas sizes kept), which
+ * gfdeconv_opts.tune_cache reads at create.  Synchronises `stream`.  Returns
+ * GFD_ERR_INVALID_ARG for a malformed existing file or one that cannot be
+ * written. */
+int gfdeconv_autotune(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs, int iters,
+                      const char* path, void* stream);
+
+/* Read a tile-shape file without a GPU (host only): *chains receives its
+ * chain count (4 if it names none), *n_classes the number of canvas sizes it
+ * holds, and the first max_classes of them go to shapes[5 * i + 0..4] as
+ * (M, N, col_threads, row_threads, gf_rows).  A missing file is an empty
+ * table.  Returns GFD_ERR_INVALID_ARG for a malformed file or a value outside
+ * the ranges gfdeconv_autotune searches. */
+int gfdeconv_tune_read(const char* path, int* chains, int* n_classes, int* shapes,
+                       int max_classes);
+
+/* Tile shapes the context uses for an M x N canvas (tuned or built-in) and
+ * its chain count; any output pointer may be NULL. */
+int gfdeconv_tune_get(gfdeconv_ctx* ctx, int M, int N, int* col_threads, int* row_threads,
+                      int* gf_rows, int* chains);
 
 /* Number of kernel launches the last solve issued (for instrumentation). */
 long long gfdeconv_last_launch_count(gfdeconv_ctx* ctx);

@@ -17,6 +17,7 @@ __all__ = [
     "Context", "GfdError", "lib", "library_path", "header_functions",
     "STATUS_NONCONVERGED", "STATUS_NONFINITE", "STATUS_BAD_PSF", "STATUS_BAD_RHO",
     "STATUS_PASSES_EXHAUSTED", "VAR_COMPENSATED", "VAR_FP64", "VAR_FP32", "VAR_FP32_RAW",
+    "VAR_DOUBLE_FLOAT",
     "BOUNDARY_PERIODIC", "BOUNDARY_TRUNCATED",
 ]
 
@@ -35,8 +36,9 @@ VAR_COMPENSATED = 0
 VAR_FP64 = 1
 VAR_FP32 = 2
 VAR_FP32_RAW = 3
-VAR_NAMES = {VAR_COMPENSATED: "compensated", VAR_FP64: "fp64", VAR_FP32: "fp32_shifted",
-             VAR_FP32_RAW: "fp32_raw"}
+VAR_DOUBLE_FLOAT = 4
+VAR_NAMES = {VAR_COMPENSATED: "compensated_split", VAR_FP64: "fp64", VAR_FP32: "fp32_shifted",
+             VAR_FP32_RAW: "fp32_raw", VAR_DOUBLE_FLOAT: "double_float"}
 # guided-filter window boundary (gfdeconv_opts.boundary)
 BOUNDARY_PERIODIC = 0
 BOUNDARY_TRUNCATED = 1
@@ -97,6 +99,9 @@ def _load():
         "gfdeconv_solve_batched": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp]),
         "gfdeconv_solve_batched_host": (ci, [vp, ci, ctypes.POINTER(Image), ci, vp]),
         "gfdeconv_guidfilter": (ci, [vp, vp, vp, ci, ci, ci, cd, vp, vp]),
+        "gfdeconv_guidfilter_color": (ci, [vp, vp, vp, ci, ci, ci, cd, vp, vp]),
+        "gfdeconv_pad_symmetric": (ci, [vp, vp, ci, ci, vp, ci, ci, vp]),
+        "gfdeconv_crop": (ci, [vp, vp, ci, ci, vp, ci, ci, vp]),
         "gfdeconv_fft2_r2c": (ci, [vp, vp, ci, ci, vp, vp]),
         "gfdeconv_fft2_c2r": (ci, [vp, vp, ci, ci, vp, vp]),
         "gfdeconv_fft2_r2c_noalloc": (ci, [vp, vp, ci, ci, vp, vp]),
@@ -107,6 +112,11 @@ def _load():
         "gfdeconv_strerror": (ctypes.c_char_p, [ci]),
         "gfdeconv_last_cuda_error": (ctypes.c_char_p, []),
         "gfdeconv_device_arch": (ci, [ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
+        "gfdeconv_autotune": (ci, [vp, ci, ctypes.POINTER(Image), ci, ctypes.c_char_p, vp]),
+        "gfdeconv_tune_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                    ctypes.POINTER(ci), ci]),
+        "gfdeconv_tune_get": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                   ctypes.POINTER(ci), ctypes.POINTER(ci)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -117,6 +127,21 @@ def _load():
 
 _lib = _load()
 lib = _lib
+
+
+def tune_read(path: str):
+    """Contents of a tile-shape file (host only): (chains, {(M, N):
+    (col_threads, row_threads, gf_rows)})."""
+    ch, n = ctypes.c_int(0), ctypes.c_int(0)
+    rc = _lib.gfdeconv_tune_read(path.encode(), ctypes.byref(ch), ctypes.byref(n), None, 0)
+    if rc != 0:
+        raise GfdError(rc, "gfdeconv_tune_read")
+    buf = (ctypes.c_int * (5 * max(n.value, 1)))()
+    rc = _lib.gfdeconv_tune_read(path.encode(), ctypes.byref(ch), ctypes.byref(n), buf, n.value)
+    if rc != 0:
+        raise GfdError(rc, "gfdeconv_tune_read")
+    return ch.value, {(buf[5 * i], buf[5 * i + 1]): tuple(buf[5 * i + 2:5 * i + 5])
+                      for i in range(n.value)}
 
 
 def device_arch(device: int = 0) -> tuple[int, int]:
@@ -324,6 +349,52 @@ class Context:
             raise GfdError(rc, "gfdeconv_guidfilter")
         return u
 
+    def pad_symmetric(self, y, M, N, stream=None):
+        """(m, n) CUDA tensor -> (M, N) canvas by symmetric reflection."""
+        import torch
+        m, n = y.shape
+        out = torch.empty((M, N), dtype=torch.float32, device=y.device)
+        rc = _lib.gfdeconv_pad_symmetric(self._h, _ptr(y, "y", torch.float32), m, n,
+                                         out.data_ptr(), int(M), int(N), _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_pad_symmetric")
+        return out
+
+    def crop(self, u_canvas, m, n, stream=None):
+        import torch
+        M, N = u_canvas.shape
+        out = torch.empty((m, n), dtype=torch.float32, device=u_canvas.device)
+        rc = _lib.gfdeconv_crop(self._h, _ptr(u_canvas, "u_canvas", torch.float32), M, N,
+                                out.data_ptr(), int(m), int(n), _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_crop")
+        return out
+
+    def solve_padded(self, y, h, sigma, w, eps, iters, stream=None):
+        """An observation of any size up to 4096 x 4096: padded to the next
+        power-of-two canvas (gfdeconv_pad_symmetric), solved there, cropped
+        back.  Returns (u (m, n), lambda[iters])."""
+        m, n = y.shape
+        M, N = 1 << max(3, (m - 1).bit_length()), 1 << max(3, (n - 1).bit_length())
+        yc = self.pad_symmetric(y, M, N, stream)
+        uc, lam, _ = self.solve(yc, h, sigma, w, eps, iters, stream=stream)
+        return self.crop(uc, m, n, stream), lam
+
+    def guidfilter_color(self, I, p, w, eps, stream=None, out=None):
+        """Colour guidance: I is a (3, M, N) float32 CUDA tensor, p (M, N)."""
+        import torch
+        C, M, N = I.shape
+        if C != 3:
+            raise ValueError("I must have 3 channels (3, M, N)")
+        u = torch.empty((M, N), dtype=torch.float32, device=p.device) if out is None else out
+        rc = _lib.gfdeconv_guidfilter_color(self._h, _ptr(I, "I", torch.float32),
+                                            _ptr(p, "p", torch.float32, M * N), M, N, int(w),
+                                            float(eps), _ptr(u, "u", torch.float32, M * N),
+                                            _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_guidfilter_color")
+        return u
+
     def fft2_r2c(self, x, stream=None):
         """Packed half spectrum as a complex64 (M, N/2) tensor."""
         import torch
@@ -356,6 +427,21 @@ class Context:
         if rc != 0:
             raise GfdError(rc, "gfdeconv_fft2_c2r")
         return x
+
+    def autotune(self, arr, iters, path=None, stream=None):
+        """gfdeconv_autotune over the descriptors `arr` (see make_images)."""
+        rc = _lib.gfdeconv_autotune(self._h, len(arr), arr, int(iters),
+                                    path.encode() if path else None, _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_autotune")
+
+    def tune_get(self, M, N):
+        """(col_threads, row_threads, gf_rows, chains) used for an M x N canvas."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        rc = _lib.gfdeconv_tune_get(self._h, int(M), int(N), *[ctypes.byref(x) for x in v])
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_tune_get")
+        return tuple(x.value for x in v)
 
     def status(self, n):
         arr = (ctypes.c_int * n)()

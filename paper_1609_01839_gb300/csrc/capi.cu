@@ -5,8 +5,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "launch.h"
@@ -49,6 +51,7 @@ struct Plan {
   // chains over parts of every class, so that the blocks of different phases
   // share the SMs (a kernel's tail overlaps the next kernel of another chain)
   std::vector<ClassLaunch> parts[CHAINS];
+  int nparts = CHAINS;
   std::vector<ImgDesc> h_imgs;           // internal order
   std::vector<gfdeconv_image> user;      // internal order
   cudaGraphExec_t exec = nullptr;
@@ -59,6 +62,8 @@ struct Plan {
 struct Timer {
   std::vector<cudaEvent_t> ev;   // 2 per launch
   std::vector<int> phase;
+  std::vector<int> cls;          // class index of each launch (-1: none)
+  int cur_cls = -1;
   size_t used = 0;
   cudaError_t begin(cudaStream_t s, int ph) {
     if (2 * used + 2 > ev.size()) {
@@ -69,8 +74,12 @@ struct Timer {
         ev.push_back(e);
       }
     }
-    if (phase.size() <= used) phase.resize(used + 1);
+    if (phase.size() <= used) {
+      phase.resize(used + 1);
+      cls.resize(used + 1);
+    }
     phase[used] = ph;
+    cls[used] = cur_cls;
     return cudaEventRecord(ev[2 * used], s);
   }
   cudaError_t end(cudaStream_t s) {
@@ -80,6 +89,29 @@ struct Timer {
   }
   ~Timer() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+// Tile shapes of one canvas size (see gfdeconv_autotune).
+struct ClassTune {
+  int M, N, col_threads, row_threads, gf_rows;
+};
+
+struct TuneTable {
+  int chains = CHAINS;  // concurrent chains of a captured solve (1..CHAINS)
+  std::vector<ClassTune> cls;
+  ClassTune get(int M, int N) const {
+    for (const ClassTune& t : cls)
+      if (t.M == M && t.N == N) return t;
+    return ClassTune{M, N, DEF_COL_THREADS, DEF_ROW_THREADS, DEF_GF_ROWS};
+  }
+  void set(const ClassTune& t) {
+    for (ClassTune& u : cls)
+      if (u.M == t.M && u.N == t.N) {
+        u = t;
+        return;
+      }
+    cls.push_back(t);
   }
 };
 
@@ -119,6 +151,7 @@ struct gfdeconv_ctx {
   size_t stage_bytes = 0;
   char* hstage = nullptr;  // pinned host staging of the small per-image arrays
   size_t hstage_bytes = 0;
+  TuneTable tune;          // tile shapes per canvas size
 };
 
 namespace {
@@ -256,7 +289,11 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
     cl.cd.N = sizes[ci].second;
     cl.cd.n_img = (int)members[ci].size();
     cl.cd.img0 = (int)pl.order.size();
-    cl.cd.TB = class_tile_width(cl.cd.M, cl.cd.N);
+    const ClassTune tn = c->tune.get(cl.cd.M, cl.cd.N);
+    cl.cd.TB = class_tile_width(cl.cd.M, cl.cd.N, tn.col_threads);
+    cl.row_threads = tn.row_threads;
+    cl.gf_rows = tn.gf_rows;
+    cl.class_id = (int)ci;
     cl.imgs = c->d_imgs;
     cl.st = c->d_st;
     cl.max_rad = 0;
@@ -316,10 +353,12 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
   // parts: CHAINS consecutive runs of the images of every class, with their
   // window-radius groups cut to the range
   for (auto& v : pl.parts) v.clear();
+  const int nparts = std::max(1, std::min(CHAINS, c->tune.chains));
+  pl.nparts = nparts;
   for (const ClassLaunch& cl : pl.classes) {
-    for (int part = 0; part < CHAINS; ++part) {
-      const int lo = cl.cd.img0 + (int)((long long)cl.cd.n_img * part / CHAINS);
-      const int hi = cl.cd.img0 + (int)((long long)cl.cd.n_img * (part + 1) / CHAINS);
+    for (int part = 0; part < nparts; ++part) {
+      const int lo = cl.cd.img0 + (int)((long long)cl.cd.n_img * part / nparts);
+      const int hi = cl.cd.img0 + (int)((long long)cl.cd.n_img * (part + 1) / nparts);
       if (hi <= lo) continue;
       ClassLaunch q = cl;
       q.cd.img0 = lo;
@@ -380,15 +419,18 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   auto setup = [&](std::vector<ClassLaunch>& classes, cudaStream_t q) -> cudaError_t {
     cudaStream_t s = q;  // the GFD_T macro records on `s`
     for (auto& cl : classes) {
+      if (tm) tm->cur_cls = cl.class_id;
       GFD_T(GFD_PHASE_COPY, launch_init_u(cl, s));  // u_E = u_init or 0
       GFD_T(GFD_PHASE_SETUP, launch_setup_stats(cl, s));
       L += 2;
     }
     for (auto& cl : classes) {
+      if (tm) tm->cur_cls = cl.class_id;
       GFD_T(GFD_PHASE_SETUP, launch_setup_init(cl, c->opts.rho, s));
       L += 2;  // k_setup_init, k_zero_parts
     }
     for (auto& cl : classes) {
+      if (tm) tm->cur_cls = cl.class_id;
       GFD_T(GFD_PHASE_SETUP, launch_embed_psf(cl, SEL_UI, s));
       // H and Y in double-float, rounded once (they fix the residual of Eq. 10-11)
       GFD_T(GFD_PHASE_SETUP, launch_fft2_r2c_df(cl, t.twdf, SEL_UI, SEL_H, s));
@@ -403,16 +445,19 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     cudaStream_t s = q;  // the GFD_T macro records on `s`
     for (int k = 0; k < pl.iters; ++k) {
       for (auto& cl : classes) {
+        if (tm) tm->cur_cls = cl.class_id;
         GFD_T(GFD_PHASE_ROW_FWD, launch_row_r2c(cl, t, SEL_U, SEL_S, true, s));
         GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
         L += 2;
       }
       for (int p = 1; p <= passes; ++p)
         for (auto& cl : classes) {
+          if (tm) tm->cur_cls = cl.class_id;
           GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == passes, s));
           ++L;
         }
       for (auto& cl : classes) {
+        if (tm) tm->cur_cls = cl.class_id;
         GFD_T(GFD_PHASE_COL_SOLVE_INV, launch_col_solve_inv(cl, t, s));
         GFD_T(GFD_PHASE_ROW_INV, launch_row_c2r(cl, t, SEL_QI, SEL_QP, SEL_UI, SEL_UP,
                                                 1.0f / ((float)cl.cd.M * (float)cl.cd.N), s));
@@ -422,14 +467,15 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     }
     return cudaSuccess;
   };
-  if (chains && !tm && CHAINS > 1 && !pl.parts[1].empty()) {
+  if (tm) tm->cur_cls = -1;
+  if (chains && !tm && pl.nparts > 1 && !pl.parts[1].empty()) {
     GFD_CK(cudaEventRecord(c->ev_fork, s));
-    for (int q = 1; q < CHAINS; ++q) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_fork, 0));
+    for (int q = 1; q < pl.nparts; ++q) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_fork, 0));
     GFD_CK(issue_imgs(pl.parts[0], true, s));
     GFD_CK(setup(pl.parts[0], s));
     GFD_CK(iterate(pl.parts[0], s));
     GFD_CK(issue_imgs(pl.parts[0], false, s));
-    for (int q = 1; q < CHAINS; ++q) {
+    for (int q = 1; q < pl.nparts; ++q) {
       GFD_CK(issue_imgs(pl.parts[q], true, c->side[q - 1]));
       GFD_CK(setup(pl.parts[q], c->side[q - 1]));
       GFD_CK(iterate(pl.parts[q], c->side[q - 1]));
@@ -559,6 +605,62 @@ int solve_batched_dev(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int it
   return map_err(e);
 }
 
+// Tile-shape file: text lines "chains C" and
+// "class M N col_threads CT row_threads RT gf_rows GR"; '#' starts a comment.
+// A missing file is an empty table.  Returns false on a malformed line or a
+// value outside the kernels' ranges.
+bool valid_tune(const ClassTune& t) {
+  auto p2 = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
+  return p2(t.M, 8, 4096) && p2(t.N, 8, 4096) && p2(t.col_threads, 32, 256) &&
+         p2(t.row_threads, 32, 256) && p2(t.gf_rows, 16, 64);
+}
+
+bool load_tune(const char* path, TuneTable* out) {
+  TuneTable t;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) {
+    *out = t;
+    return true;
+  }
+  char line[256];
+  bool ok = true;
+  while (ok && std::fgets(line, sizeof line, f)) {
+    char* h = std::strchr(line, '#');
+    if (h) *h = 0;
+    char word[32] = {0};
+    if (std::sscanf(line, "%31s", word) != 1) continue;  // blank
+    if (!std::strcmp(word, "chains")) {
+      int q = 0;
+      ok = std::sscanf(line, "%*s %d", &q) == 1 && q >= 1 && q <= CHAINS;
+      if (ok) t.chains = q;
+    } else if (!std::strcmp(word, "class")) {
+      ClassTune c{};
+      ok = std::sscanf(line, "%*s %d %d col_threads %d row_threads %d gf_rows %d", &c.M, &c.N,
+                       &c.col_threads, &c.row_threads, &c.gf_rows) == 5 &&
+           valid_tune(c);
+      if (ok) t.set(c);
+    } else {
+      ok = false;
+    }
+  }
+  std::fclose(f);
+  if (ok) *out = t;
+  return ok;
+}
+
+bool save_tune(const char* path, const TuneTable& t) {
+  const std::string tmp = std::string(path) + ".tmp";
+  std::FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  std::fprintf(f, "# gfdeconv tile shapes, written by gfdeconv_autotune\n");
+  std::fprintf(f, "chains %d\n", t.chains);
+  for (const ClassTune& c : t.cls)
+    std::fprintf(f, "class %d %d col_threads %d row_threads %d gf_rows %d\n", c.M, c.N,
+                 c.col_threads, c.row_threads, c.gf_rows);
+  const bool ok = std::fclose(f) == 0;
+  return ok && std::rename(tmp.c_str(), path) == 0;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -591,7 +693,7 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   if (cuda_device < 0 || cuda_device >= ndev) return GFD_ERR_INVALID_ARG;
   if (opts) {
     if (opts->rho > 1.0 || !std::isfinite(opts->rho)) return GFD_ERR_INVALID_ARG;
-    if (opts->var_precision < GFD_VAR_COMPENSATED || opts->var_precision > GFD_VAR_FP32_RAW)
+    if (opts->var_precision < GFD_VAR_COMPENSATED || opts->var_precision > GFD_VAR_DOUBLE_FLOAT)
       return GFD_ERR_INVALID_ARG;
     if (opts->boundary != GFD_BOUNDARY_PERIODIC && opts->boundary != GFD_BOUNDARY_TRUNCATED)
       return GFD_ERR_INVALID_ARG;
@@ -599,8 +701,10 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
     if (!std::isfinite(opts->lambda_rtol) ||
         (opts->lambda_rtol > 0.0 && (opts->lambda_rtol < 1e-14 || opts->lambda_rtol > 1e-2)))
       return GFD_ERR_INVALID_ARG;
-    if (opts->tune_cache && opts->tune_cache[0]) return GFD_ERR_INVALID_ARG;
   }
+  TuneTable tune;
+  if (opts && opts->tune_cache && opts->tune_cache[0] && !load_tune(opts->tune_cache, &tune))
+    return GFD_ERR_INVALID_ARG;
   if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) return map_err(e);
   gfdeconv_ctx* c = new (std::nothrow) gfdeconv_ctx();
   if (!c) return GFD_ERR_ALLOC;
@@ -616,6 +720,7 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   if (c->opts.lambda_max_passes <= 0) c->opts.lambda_max_passes = LAMBDA_FALLBACK_PASSES;
   if (c->opts.lambda_rtol <= 0.0) c->opts.lambda_rtol = 1e-13;
   c->opts.tune_cache = nullptr;  // not retained
+  c->tune = tune;
   e = configure_kernels();
   if (e != cudaSuccess) {
     delete c;
@@ -706,6 +811,163 @@ int gfdeconv_solve_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, i
   }
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
   return solve_batched_dev(c, n, imgs, iters, (cudaStream_t)stream);
+}
+
+int gfdeconv_autotune(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
+                      const char* path, void* stream) {
+  if (!c || !imgs || n <= 0) return GFD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    int r = validate_image(imgs[i], iters);
+    if (r == GFD_OK) r = validate_device_planes(imgs[i]);
+    if (r != GFD_OK) return r;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  TuneTable saved = c->tune;
+  if (path && path[0] && !load_tune(path, &saved)) return GFD_ERR_INVALID_ARG;
+  // the batch's canvas sizes, in order of first appearance (build_plan's order)
+  std::vector<std::pair<int, int>> sizes;
+  for (int i = 0; i < n; ++i) {
+    const std::pair<int, int> sz(imgs[i].M, imgs[i].N);
+    if (std::find(sizes.begin(), sizes.end(), sz) == sizes.end()) sizes.push_back(sz);
+  }
+  TuneTable cur = saved;
+  for (const auto& sz : sizes) cur.set(cur.get(sz.first, sz.second));
+  // Event-timed direct launches of the whole solve; per class and phase, the
+  // summed device milliseconds of the second of two runs.
+  auto measure = [&](std::vector<std::vector<double>>* per) -> cudaError_t {
+    c->tune = cur;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    drop_plan(c);
+    if ((e = build_plan(c, n, imgs, iters)) != cudaSuccess) return e;
+    c->have_plan = true;
+    c->plan.key = make_key(c, n, imgs, iters);
+    for (int rep = 0; rep < 2; ++rep) {
+      Timer tm;
+      if ((e = record(c, c->plan, s, &tm)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      if (rep == 0) continue;
+      per->assign(sizes.size(), std::vector<double>(GFD_NUM_PHASES, 0.0));
+      for (size_t i = 0; i < tm.used; ++i) {
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, tm.ev[2 * i], tm.ev[2 * i + 1])) != cudaSuccess) return e;
+        const int ci = tm.cls[i], ph = tm.phase[i];
+        if (ci >= 0 && ci < (int)sizes.size() && ph >= 0 && ph < GFD_NUM_PHASES)
+          (*per)[ci][ph] += ms;
+      }
+    }
+    return cudaSuccess;
+  };
+  auto fail = [&](cudaError_t e) {
+    c->tune = saved;
+    drop_plan(c);
+    return map_err(e);
+  };
+  // one shape at a time: every class takes each candidate together; each
+  // class keeps its fastest over the phases the shape affects
+  struct Axis {
+    int ClassTune::*field;
+    std::vector<int> cand;
+    std::vector<int> phases;
+  };
+  const std::vector<Axis> axes = {
+      {&ClassTune::col_threads, {64, 128, 256},
+       {GFD_PHASE_ROW_FWD, GFD_PHASE_COL_FWD_LAMBDA, GFD_PHASE_LAMBDA_PASS, GFD_PHASE_COL_SOLVE_INV,
+        GFD_PHASE_ROW_INV}},
+      {&ClassTune::row_threads, {64, 128, 256},
+       {GFD_PHASE_ROW_FWD, GFD_PHASE_COL_FWD_LAMBDA, GFD_PHASE_ROW_INV}},
+      {&ClassTune::gf_rows, {16, 32, 64}, {GFD_PHASE_GUIDED_FILTER}}};
+  for (const Axis& ax : axes) {
+    std::vector<double> best(sizes.size(), 1e300);
+    std::vector<int> pick(sizes.size(), 0);
+    for (size_t ci = 0; ci < sizes.size(); ++ci) pick[ci] = cur.get(sizes[ci].first, sizes[ci].second).*(ax.field);
+    for (int v : ax.cand) {
+      for (const auto& sz : sizes) {
+        ClassTune t = cur.get(sz.first, sz.second);
+        t.*(ax.field) = v;
+        cur.set(t);
+      }
+      std::vector<std::vector<double>> per;
+      const cudaError_t e = measure(&per);
+      if (e != cudaSuccess) return fail(e);
+      for (size_t ci = 0; ci < sizes.size(); ++ci) {
+        double ms = 0.0;
+        for (int ph : ax.phases) ms += per[ci][ph];
+        if (ms < best[ci]) {
+          best[ci] = ms;
+          pick[ci] = v;
+        }
+      }
+    }
+    for (size_t ci = 0; ci < sizes.size(); ++ci) {
+      ClassTune t = cur.get(sizes[ci].first, sizes[ci].second);
+      t.*(ax.field) = pick[ci];
+      cur.set(t);
+    }
+  }
+  // concurrent chains of the captured solve: graph replays timed on `s`
+  if (c->opts.use_graphs) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e300;
+    int pick = cur.chains;
+    for (int q = 1; q <= CHAINS && e == cudaSuccess; q *= 2) {
+      cur.chains = q;
+      c->tune = cur;
+      drop_plan(c);
+      const int r = solve_batched_dev(c, n, imgs, iters, s);  // builds and captures
+      if (r != GFD_OK) {
+        e = g_last_cuda_error == cudaSuccess ? cudaErrorUnknown : g_last_cuda_error;
+        break;
+      }
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphLaunch(c->plan.exec, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        pick = q;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(e);
+    cur.chains = pick;
+  }
+  c->tune = cur;
+  drop_plan(c);
+  if (path && path[0] && !save_tune(path, cur)) return GFD_ERR_INVALID_ARG;
+  return GFD_OK;
+}
+
+int gfdeconv_tune_read(const char* path, int* chains, int* n_classes, int* shapes,
+                       int max_classes) {
+  if (!path) return GFD_ERR_INVALID_ARG;
+  TuneTable t;
+  if (!load_tune(path, &t)) return GFD_ERR_INVALID_ARG;
+  if (chains) *chains = t.chains;
+  if (n_classes) *n_classes = (int)t.cls.size();
+  for (int i = 0; shapes && i < max_classes && i < (int)t.cls.size(); ++i) {
+    const ClassTune& c = t.cls[i];
+    const int v[5] = {c.M, c.N, c.col_threads, c.row_threads, c.gf_rows};
+    std::memcpy(shapes + 5 * i, v, sizeof v);
+  }
+  return GFD_OK;
+}
+
+int gfdeconv_tune_get(gfdeconv_ctx* c, int M, int N, int* col_threads, int* row_threads,
+                      int* gf_rows, int* chains) {
+  if (!c) return GFD_ERR_INVALID_ARG;
+  const ClassTune t = c->tune.get(M, N);
+  if (col_threads) *col_threads = t.col_threads;
+  if (row_threads) *row_threads = t.row_threads;
+  if (gf_rows) *gf_rows = t.gf_rows;
+  if (chains) *chains = c->tune.chains;
+  return GFD_OK;
 }
 
 int gfdeconv_solve_batched_timed(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int iters,
@@ -998,7 +1260,48 @@ int gfdeconv_guidfilter(gfdeconv_ctx* c, const float* I, const float* p, int M, 
   cl.max_rad = (w - 1) / 2;
   cl.n_rad_groups = 1;
   cl.rad_groups[0] = RadGroup{0, 1, (w - 1) / 2};
+  if (c->opts.var_precision == GFD_VAR_COMPENSATED) {  // the split sums' bound
+    if ((e = cudaMemsetAsync(c->aux_st->absmax, 0, sizeof(c->aux_st->absmax), s)) != cudaSuccess ||
+        (e = launch_plane_absmax(cl, s)) != cudaSuccess)
+      return map_err(e);
+  }
   if ((e = launch_guided_filter(cl, -1, c->opts.var_precision, c->opts.boundary, s)) != cudaSuccess)
+    return map_err(e);
+  return map_err(aux_finish(a, s));
+}
+
+int gfdeconv_pad_symmetric(gfdeconv_ctx* c, const float* y, int m, int n, float* y_canvas, int M,
+                           int N, void* stream) {
+  if (!c || !y || !y_canvas) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (m < 1 || n < 1 || m > M || n > N) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  return map_err(launch_pad_symmetric(y, m, n, y_canvas, M, N, (cudaStream_t)stream));
+}
+
+int gfdeconv_crop(gfdeconv_ctx* c, const float* u_canvas, int M, int N, float* u, int m, int n,
+                  void* stream) {
+  if (!c || !u_canvas || !u) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (m < 1 || n < 1 || m > M || n > N) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  return map_err(launch_crop(u_canvas, N, u, m, n, (cudaStream_t)stream));
+}
+
+int gfdeconv_guidfilter_color(gfdeconv_ctx* c, const float* I, const float* p, int M, int N,
+                              int w, double eps, float* u_out, void* stream) {
+  if (!c || !I || !p || !u_out) return GFD_ERR_INVALID_ARG;
+  if (!aligned16(I) || !aligned16(p) || !aligned16(u_out)) return GFD_ERR_INVALID_ARG;
+  if (!pow2_in(M, 8, 4096) || !pow2_in(N, 8, 4096)) return GFD_ERR_UNSUPPORTED_SIZE;
+  if (!std::isfinite(eps)) return GFD_ERR_NONFINITE_INPUT;
+  if (!(eps > 0.0) || w < 1 || w > 17 || !(w & 1)) return GFD_ERR_INVALID_ARG;
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  AuxSlot* a = nullptr;
+  cudaError_t e = aux_slot(c, (size_t)4 * M * N * sizeof(float), &a);
+  if (e != cudaSuccess) return map_err(e);
+  if ((e = launch_guided_filter_color(I, p, M, N, w, eps, c->opts.boundary,
+                                      reinterpret_cast<float*>(a->ws), u_out, s)) != cudaSuccess)
     return map_err(e);
   return map_err(aux_finish(a, s));
 }

@@ -58,6 +58,15 @@ GFD_D float warp_sum(float v) {
     if ((unsigned)o < n) v += __shfl_xor_sync(mask, v, o);
   return v;
 }
+// Maximum over the threads of a warp (same partial-warp rule as warp_sum).
+GFD_D float warp_max(float v) {
+  const unsigned int n = blockDim.x < 32 ? blockDim.x : 32u;
+  const unsigned int mask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    if ((unsigned)o < n) v = fmaxf(v, __shfl_xor_sync(mask, v, o));
+  return v;
+}
 GFD_D int num_warps() { return (int)((blockDim.x + 31) >> 5); }
 
 // Asynchronous global -> shared copies (16-byte chunks, L2 only) with
@@ -113,6 +122,7 @@ struct ImgState {
   int iter;          // iteration index of the pending outputs
   int pad_;
   double rtol;       // relative width of lambda at which the root search stops
+  unsigned int absmax[2];  // bits of max |u_I|, max |u_p| of the current iteration
 };
 
 // Per-image parameters and pointers, device memory.

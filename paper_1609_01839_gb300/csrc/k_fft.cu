@@ -52,6 +52,9 @@ constexpr int SMEM_TW_MAX = 1024;
 // X[k] = (Z[k] + conj Z[-k])/2 + W_N^k (Z[k] - conj Z[-k])/(2i), and
 // X[0], X[N/2] = Re Z[0] +- Im Z[0] (packed as X[0] + i X[N/2]).
 // ---------------------------------------------------------------------------
+// float2 elements of the row-pass work area of rpc teams, rounded up to even.
+GFD_HD int row_work_elems(int L, int rpc) { return (rpc * team_stride(L) + 1) & ~1; }
+
 template <int L>
 __global__ void __launch_bounds__(256, 2)
 k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restrict__ tw, int rpc,
@@ -63,7 +66,9 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
   const int item_elems = rpc * L;
   float2* land = smem;
   float2* work = land + item_elems;
-  float2* outb = work + rpc * team_stride(L);
+  // team_stride(L) is odd: round the work area up to an even number of float2
+  // so that the output rows (read as 16-byte vectors) start 16-byte aligned
+  float2* outb = work + row_work_elems(L, rpc);
   double* red = reinterpret_cast<double*>(outb + item_elems);
   // length-L twiddle table in shared memory (L <= SMEM_TW_MAX)
   const float2* twL = tw + tab_off(L);
@@ -151,7 +156,7 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
 template <int L>
 __global__ void __launch_bounds__(256, 3)
 k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restrict__ tw, int rpc,
-          int sel0, int sel1, int dsel0, int dsel1, float scale) {
+          int sel0, int sel1, int dsel0, int dsel1, float scale, ImgState* st) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(L), T = threads_per_team(L);
   constexpr int N = 2 * L;
@@ -224,10 +229,20 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
     issue(item + gridDim.x);
     fft_team<L, true>(buf, j, twL);
     float2* rowp = reinterpret_cast<float2*>(real_plane(d, dsel)) + (size_t)row * L;
+    float amax = 0.0f;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int n = j + i * T;
-      rowp[n] = cscale(buf[phys(out_pos<L>(n))], scale);
+      const float2 v = cscale(buf[phys(out_pos<L>(n))], scale);
+      rowp[n] = v;
+      amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    // largest |value| of the plane (u_I, u_p): bounds the guided filter's
+    // split window sums; non-negative floats order like their bit patterns
+    if (st) {
+      amax = warp_max(amax);  // the teams of a warp share one image and plane
+      if ((threadIdx.x & 31) == 0)
+        atomicMax(&st[cd.img0 + li].absmax[dsel == dsel0 ? 0 : 1], __float_as_uint(amax));
     }
   }
   cp_async_wait<0>();
@@ -578,7 +593,7 @@ GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool bra
 // while the next item's tile is fetched.
 template <int M>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
-k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* st,
+k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                 const float2* __restrict__ tw, const float* __restrict__ d2tab) {
   extern __shared__ __align__(16) float2 smem[];
   constexpr int R = radix_for(M), T = threads_per_team(M);
@@ -620,6 +635,10 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, const ImgState* 
     const size_t off = (size_t)t * tile;
     const double lamd = __ldcg(&st[gi].lam);
     const bool branch = !(lamd < 1e300);
+    if (t == 0 && threadIdx.x == 0) {  // the inverse row pass re-forms them
+      st[gi].absmax[0] = 0u;
+      st[gi].absmax[1] = 0u;
+    }
     const float lam = branch ? 0.0f : (float)lamd;
     const float d2c = __ldg(&d2tab[tab_off(N) + col]);
     float2* bufI = workI + b * ts;
@@ -701,22 +720,21 @@ static int persistent_grid(K kernel, int threads, size_t smem, int n_items, int 
   return (int)(g < n_items ? g : n_items);
 }
 
-TileConfig g_tiles;
-
-static int rows_per_item(int L, int M) {
+int rows_per_item(int L, int M, int row_threads) {
   const int T = threads_per_team(L);
-  int r = g_tiles.row_threads / T;
+  int r = (row_threads > 0 ? row_threads : DEF_ROW_THREADS) / T;
   if (r < 1) r = 1;
   if (r > M) r = M;
   return r;
 }
 
 // Tile width of a class's spectra = columns per column item: a block of about
-// g_tiles.col_threads threads (512 for M = 4096), at least 2 columns (16-byte
+// col_threads threads (512 for M = 4096), at least 2 columns (16-byte
 // copies), at most N/2.
-int class_tile_width(int M, int N) {
+int class_tile_width(int M, int N, int col_threads) {
   const int T = M / radix_for(M);
-  const int threads = M >= 4096 ? 512 : g_tiles.col_threads;
+  const int ct = col_threads > 0 ? (col_threads > 256 ? 256 : col_threads) : DEF_COL_THREADS;
+  const int threads = M >= 4096 ? 512 : ct;
   int B = threads / T;
   if (B < 2) B = 2;
   if (B > N / 2) B = N / 2;
@@ -724,7 +742,7 @@ int class_tile_width(int M, int N) {
 }
 
 static size_t row_r2c_smem(int L, int rpc) {
-  return (size_t)2 * rpc * L * sizeof(float2) + (size_t)rpc * team_stride(L) * sizeof(float2) +
+  return (size_t)2 * rpc * L * sizeof(float2) + (size_t)row_work_elems(L, rpc) * sizeof(float2) +
          32 * sizeof(double) + (L <= SMEM_TW_MAX ? (size_t)L * sizeof(float2) : 0);
 }
 static size_t row_c2r_smem(int L, int rpc) {
@@ -759,7 +777,7 @@ static size_t row_c2r_smem(int L, int rpc) {
 template <int L>
 static void do_row_r2c(const ClassLaunch& c, const Tables& t, int src, int dst, int sum,
                        cudaStream_t s) {
-  const int rpc = rows_per_item(L, c.cd.M);
+  const int rpc = rows_per_item(L, c.cd.M, c.row_threads);
   const int n_items = c.cd.n_img * c.cd.M / rpc;
   const int thr = rpc * threads_per_team(L);
   const size_t smem = row_r2c_smem(L, rpc);
@@ -779,13 +797,14 @@ cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int d
 template <int L>
 static void do_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
                        int dsel1, float scale, cudaStream_t s) {
-  const int rpc = rows_per_item(L, c.cd.M);
+  const int rpc = rows_per_item(L, c.cd.M, c.row_threads);
   int n_items = c.cd.n_img * c.cd.M / rpc;
   if (sel1 >= 0) n_items *= 2;
   const int thr = rpc * threads_per_team(L);
   const size_t smem = row_c2r_smem(L, rpc);
   const int grid = persistent_grid(k_row_c2r<L>, thr, smem, n_items, c.grid_div);
-  k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, dsel0, dsel1, scale);
+  k_row_c2r<L><<<grid, thr, smem, s>>>(c.cd, c.imgs, t.tw, rpc, sel0, sel1, dsel0, dsel1, scale,
+                                       dsel0 == SEL_UI ? c.st : nullptr);
 }
 
 cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
@@ -839,7 +858,7 @@ static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, c
   const size_t smem = col_smem<M>(B, 1, 1, nthr);
   const int n_items = c.cd.n_img * (Lc / B);
   const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items, c.grid_div);
-  const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M);
+  const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M, c.row_threads);
   k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, iter, row_items);
 }
 

@@ -31,6 +31,8 @@
 // accumulators, or plain FP32.  sigma_k^2 and the covariance are then formed
 // as (n S_JJ - S_J^2) / n^2 and (n S_JQ - S_J S_Q) / n^2 in that arithmetic
 // and rounded to FP32 once.
+#include <type_traits>
+
 #include "common.cuh"
 #include "df.cuh"
 #include "launch.h"
@@ -97,6 +99,49 @@ struct SumDF {
     lo += t.lo + e;
   }
 };
+
+// Split sums.  Every deviation x (J or Q) is split on a power-of-two grid g
+// chosen per item from a bound on |x| (g >= 2^-11 max |x|): x = g m + x_l with
+// m = round(x / g), |m| <= 2^11, and x_l = x - g m (exact).  Window sums of m,
+// m_J^2 and m_J m_Q are exact in int32 (|m m'| <= 2^22, at most 289 terms, on
+// the integer pipe); the remainders' parts, x_l, J^2 - (g_J m_J)^2 =
+// J_l (J + g_J m_J) and J Q - g_J m_J g_Q m_Q = g_J m_J Q_l + J_l Q, are
+// summed in FP32, where their rounding is 2^-11 of that of plain sums.
+struct SumIG {
+  static constexpr int kSub = 1 << 30;
+  int h;
+  float l;
+};
+
+// The grids of one item: g, 1/g and g * kMagic for J and for Q.
+struct IGGrid {
+  float gJ, igJ, mgJ, gQ, igQ, mgQ;
+};
+
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
+
+GFD_D void ig_grid(float bound, float& g, float& ig, float& mg) {
+  int e = 0;
+  if (bound > 0.0f && bound < 3e38f) frexpf(bound, &e);  // bound <= 2^e
+  if (e < -100) e = -100;
+  g = ldexpf(1.0f, e - 11);
+  ig = ldexpf(1.0f, 11 - e);
+  mg = kMagic * g;
+}
+
+// x = g m + xl: m = round(x / g) (kMagic + x / g rounds to an integer-valued
+// float whose low bits are m), g m exact, xl = x - g m exact.
+GFD_D void ig_split(float x, float ig, float g, float mg, int& m, float& xh, float& xl) {
+  const float t = fmaf(x, ig, kMagic);
+  m = __float_as_int(t) - __float_as_int(kMagic);
+  xh = fmaf(t, g, -mg);
+  xl = x - xh;
+}
+
+// int32 |v| < 2^22 to float, exactly, without a conversion instruction
+GFD_D float small_int_to_float(int v) {
+  return __int_as_float(__float_as_int(kMagic) + v) - kMagic;
+}
 
 // Value of lane (lane + off) (compile-time offset after unrolling).
 template <class T>
@@ -193,11 +238,27 @@ GFD_D void hsum4(const SumDF (&v)[4], SumDF (&s)[4]) {
   }
 }
 
+template <int RAD>
+GFD_D void hsum4(const SumIG (&v)[4], SumIG (&s)[4]) {
+  const int ih[4] = {v[0].h, v[1].h, v[2].h, v[3].h};
+  const float il[4] = {v[0].l, v[1].l, v[2].l, v[3].l};
+  int oh[4];
+  float ol[4];
+  hsum4_scalar<RAD>(ih, oh);
+  hsum4_scalar<RAD>(il, ol);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s[k].h = oh[k];
+    s[k].l = ol[k];
+  }
+}
+
 // Means and (co)variance of a window of n pixels from S = (sum J, sum Q,
 // sum J^2, sum J Q):  var = (n S_JJ - S_J^2) / n^2 (sigma_k^2, the
 // population variance), cov = (n S_JQ - S_J S_Q) / n^2.
 GFD_D void window_stats(const SumF32& s0, const SumF32& s1, const SumF32& s2, const SumF32& s3,
-                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+                        float n, float inv_n, const IGGrid&, float& mJ, float& mQ, float& var,
+                        float& cov) {
   (void)n;
   mJ = s0.v * inv_n;
   mQ = s1.v * inv_n;
@@ -206,7 +267,8 @@ GFD_D void window_stats(const SumF32& s0, const SumF32& s1, const SumF32& s2, co
 }
 
 GFD_D void window_stats(const SumF64& s0, const SumF64& s1, const SumF64& s2, const SumF64& s3,
-                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+                        float n, float inv_n, const IGGrid&, float& mJ, float& mQ, float& var,
+                        float& cov) {
   (void)inv_n;
   const double nn = (double)n, inv2 = 1.0 / (nn * nn);
   mJ = (float)(s0.v / nn);
@@ -216,7 +278,8 @@ GFD_D void window_stats(const SumF64& s0, const SumF64& s1, const SumF64& s2, co
 }
 
 GFD_D void window_stats(const SumDF& s0, const SumDF& s1, const SumDF& s2, const SumDF& s3,
-                        float n, float inv_n, float& mJ, float& mQ, float& var, float& cov) {
+                        float n, float inv_n, const IGGrid&, float& mJ, float& mQ, float& var,
+                        float& cov) {
   const df S0{s0.hi, s0.lo}, S1{s1.hi, s1.lo}, S2{s2.hi, s2.lo}, S3{s3.hi, s3.lo};
   const df v = df_sub(df_mul_f(S2, n), df_mul(S0, S0));
   const df c = df_sub(df_mul_f(S3, n), df_mul(S0, S1));
@@ -225,6 +288,78 @@ GFD_D void window_stats(const SumDF& s0, const SumDF& s1, const SumDF& s2, const
   mQ = (s1.hi + s1.lo) * inv_n;
   var = (v.hi + v.lo) * inv2;
   cov = (c.hi + c.lo) * inv2;
+}
+
+// Split sums: the integer parts of n S_JJ - S_J^2 and n S_JQ - S_J S_Q are
+// exact in int64; the remainders' parts are added in FP32.
+GFD_D void window_stats(const SumIG& s0, const SumIG& s1, const SumIG& s2, const SumIG& s3,
+                        float n, float inv_n, const IGGrid& G, float& mJ, float& mQ, float& var,
+                        float& cov) {
+  const long long ni = (long long)(int)n;
+  const long long D = ni * s2.h - (long long)s0.h * s0.h;
+  const long long E = ni * s3.h - (long long)s0.h * s1.h;
+  const float hJ = G.gJ * small_int_to_float(s0.h);  // g_J sum m_J (exact)
+  const float hQ = G.gQ * small_int_to_float(s1.h);
+  const float lv = fmaf(n, s2.l, -fmaf(2.0f * hJ + s0.l, s0.l, 0.0f));
+  const float lc = fmaf(n, s3.l, -fmaf(hJ, s1.l, fmaf(hQ + s1.l, s0.l, 0.0f)));
+  const float inv2 = inv_n * inv_n;
+  mJ = (hJ + s0.l) * inv_n;
+  mQ = (hQ + s1.l) * inv_n;
+  var = fmaf(G.gJ * G.gJ, __ll2float_rn(D), lv) * inv2;
+  cov = fmaf(G.gJ * G.gQ, __ll2float_rn(E), lc) * inv2;
+}
+
+// Column-sum update by one input row's deviations (sign +1: the row enters,
+// -1: it leaves).
+template <class ACC>
+GFD_D void col_update(ACC (&V)[4][4], const float (&J)[4], const float (&Q)[4], float sgn,
+                      const IGGrid&) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    V[0][k].add(sgn * J[k]);
+    V[1][k].add(sgn * Q[k]);
+    V[2][k].add_prod(sgn * J[k], J[k]);
+    V[3][k].add_prod(sgn * J[k], Q[k]);
+  }
+}
+
+GFD_D void col_update(SumIG (&V)[4][4], const float (&J)[4], const float (&Q)[4], float sgn,
+                      const IGGrid& G) {
+  const int si = sgn > 0.0f ? 1 : -1;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    int mJ, mQ;
+    float Jh, Jl, Qh, Ql;
+    ig_split(J[k], G.igJ, G.gJ, G.mgJ, mJ, Jh, Jl);
+    ig_split(Q[k], G.igQ, G.gQ, G.mgQ, mQ, Qh, Ql);
+    const int smJ = si * mJ;
+    V[0][k].h += smJ;
+    V[1][k].h += si * mQ;
+    V[2][k].h += smJ * mJ;
+    V[3][k].h += smJ * mQ;
+    const float sJl = sgn * Jl;
+    V[0][k].l += sJl;
+    V[1][k].l += sgn * Ql;
+    V[2][k].l = fmaf(sJl, J[k] + Jh, V[2][k].l);
+    V[3][k].l = fmaf(sgn * Jh, Ql, fmaf(sJl, Q[k], V[3][k].l));
+  }
+}
+
+template <class ACC>
+GFD_D void col_clear(ACC (&V)[4][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) V[q][k].clear();
+}
+GFD_D void col_clear(SumIG (&V)[4][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      V[q][k].h = 0;
+      V[q][k].l = 0.0f;
+    }
 }
 
 // Pixels of the window of radius RAD about position x in [0, L) that lie in
@@ -285,6 +420,13 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       cP = __ldg(&P[c]);
     }
     const float eps = (float)d.eps;
+    IGGrid G{};
+    if constexpr (std::is_same<ACC, SumIG>::value) {
+      // |J| <= max |u_I| + |c_I| (the bound the inverse row pass recorded)
+      const ImgState* S = st + gi;
+      ig_grid(__uint_as_float(__ldcg(&S->absmax[0])) + fabsf(cI), G.gJ, G.igJ, G.mgJ);
+      ig_grid(__uint_as_float(__ldcg(&S->absmax[1])) + fabsf(cP), G.gQ, G.igQ, G.mgQ);
+    }
     // input row j of the item is image row y0 - 2r + j, ring slot j % RI
     const int nin = H + 4 * RAD;
     auto fetch = [&](int j) {
@@ -335,37 +477,19 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       if (uo && store && t >= 0)
         g = __ldg(reinterpret_cast<const float4*>(uo + (size_t)((y0 + t) & (M - 1)) * N + gx));
       if (s % ACC::kSub == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) V[q][k].clear();
+        col_clear(V);
 #pragma unroll
         for (int dd = 0; dd < WIN; ++dd) {
           float J[4], Q[4];
           devs(s + dd, J, Q);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            V[0][k].add(J[k]);
-            V[1][k].add(Q[k]);
-            V[2][k].add_prod(J[k], J[k]);
-            V[3][k].add_prod(J[k], Q[k]);
-          }
+          col_update(V, J, Q, 1.0f, G);
         }
       } else {
         float Jn[4], Qn[4], Jo[4], Qo[4];
         devs(s + 2 * RAD, Jn, Qn);
         devs(s - 1, Jo, Qo);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          V[0][k].add(Jn[k]);
-          V[0][k].add(-Jo[k]);
-          V[1][k].add(Qn[k]);
-          V[1][k].add(-Qo[k]);
-          V[2][k].add_prod(Jn[k], Jn[k]);
-          V[2][k].add_prod(-Jo[k], Jo[k]);
-          V[3][k].add_prod(Jn[k], Qn[k]);
-          V[3][k].add_prod(-Jo[k], Qo[k]);
-        }
+        col_update(V, Jn, Qn, 1.0f, G);
+        col_update(V, Jo, Qo, -1.0f, G);
       }
       // 2. row window sums -> a_k (Eq. 3), b_k (Eq. 4)
       ACC S0[4], S1[4], S2[4], S3[4];
@@ -389,9 +513,11 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
           inv_n = __frcp_rn(n);
         }
         float mJ, mQ, var, cov;
-        window_stats(S0[k], S1[k], S2[k], S3[k], n, inv_n, mJ, mQ, var, cov);
+        window_stats(S0[k], S1[k], S2[k], S3[k], n, inv_n, G, mJ, mQ, var, cov);
         A[k] = __fdividef(cov, var + eps);  // var + eps >= eps > 0
-        B[k] = (mQ + cP) - A[k] * (mJ + cI);
+        // b_k about the references: b_k = B_k + c_p - a_k c_I (Eq. 4), and the
+        // constant parts are restored in the output below
+        B[k] = fmaf(-A[k], mJ, mQ);
         if constexpr (TRUNC) {  // windows centred outside the canvas do not exist
           const float m = srow_mask * cmask[k];
           A[k] *= m;
@@ -434,12 +560,14 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
         }
       }
       // 4. row window sums of a, b -> u = abar I + bbar (Eq. 5); the guidance
-      //    at output row t is input row j = t + 2r = s
+      //    at output row t is input row j = t + 2r = s.  With b_k = B_k + c_p
+      //    - a_k c_I, u = abar (I - c_I) + Bbar + c_p: no large terms cancel
+      //    where I and p are large (small lambda amplifies noise in them)
       float SA[4], SB[4];
       hsum4<RAD>(VA[0], SA);
       hsum4<RAD>(VA[1], SB);
       const float4 iv = ring4(rI, s);
-      const float ic[4] = {iv.x, iv.y, iv.z, iv.w};
+      const float ic[4] = {iv.x - cI, iv.y - cI, iv.z - cI, iv.w - cI};
       float nout = 0.0f;
       if constexpr (TRUNC) nout = (float)window_count(y0 + t, M, RAD);
       float o[4];
@@ -447,7 +575,7 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       for (int k = 0; k < 4; ++k) {
         float inv_n = inv_full;
         if constexpr (TRUNC) inv_n = __frcp_rn(nout * ncol[k]);
-        o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n);
+        o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n) + cP;
       }
       if (store) {
         const size_t off = (size_t)((y0 + t) & (M - 1)) * N + gx;
@@ -519,8 +647,38 @@ static GfKernel gf_kernel(int var_mode, int boundary) {
     case GFD_VAR_FP64: return tr ? k_guided_filter<SumF64, true> : k_guided_filter<SumF64, false>;
     case GFD_VAR_FP32:
     case GFD_VAR_FP32_RAW: return tr ? k_guided_filter<SumF32, true> : k_guided_filter<SumF32, false>;
-    default: return tr ? k_guided_filter<SumDF, true> : k_guided_filter<SumDF, false>;
+    case GFD_VAR_DOUBLE_FLOAT:
+      return tr ? k_guided_filter<SumDF, true> : k_guided_filter<SumDF, false>;
+    default: return tr ? k_guided_filter<SumIG, true> : k_guided_filter<SumIG, false>;
   }
+}
+
+// Largest |I| and |p| of each image of a class into ImgState::absmax (the
+// bound of the split sums when no inverse row pass has recorded it).
+__global__ void k_plane_absmax(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st) {
+  const int gi = cd.img0 + blockIdx.y;
+  const ImgDesc& d = imgs[gi];
+  const size_t P = (size_t)cd.M * cd.N;
+  float mi = 0.0f, mp = 0.0f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (size_t)gridDim.x * blockDim.x) {
+    mi = fmaxf(mi, fabsf(__ldg(&d.uI[i])));
+    mp = fmaxf(mp, fabsf(__ldg(&d.up[i])));
+  }
+  mi = warp_max(mi);
+  mp = warp_max(mp);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st[gi].absmax[0], __float_as_uint(mi));
+    atomicMax(&st[gi].absmax[1], __float_as_uint(mp));
+  }
+}
+
+cudaError_t launch_plane_absmax(const ClassLaunch& c, cudaStream_t s) {
+  const size_t P = (size_t)c.cd.M * c.cd.N;
+  int chunks = (int)((P + 256 * 8 - 1) / (256 * 8));
+  if (chunks > 128) chunks = 128;
+  k_plane_absmax<<<dim3(chunks, c.cd.n_img), 256, 0, s>>>(c.cd, c.imgs, c.st);
+  return cudaGetLastError();
 }
 
 // One launch per window radius present in the class (the images of a class
@@ -545,7 +703,8 @@ cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int var_mode, i
     const int div = c.grid_div > 1 ? c.grid_div : 1;
     const int warps = (per_sm * gf_sm_count() + div - 1) / div * GFW_WARPS;
     const int strips = (cd.N + gfw_wout(rg.rad) - 1) / gfw_wout(rg.rad);
-    int H = cd.M < 64 ? cd.M : 64;
+    const int hmax = c.gf_rows > 0 ? c.gf_rows : DEF_GF_ROWS;
+    int H = cd.M < hmax ? cd.M : hmax;
     while (H > 16 && cd.n_img * strips * (cd.M / H) < warps) H /= 2;
     const int n_items = cd.n_img * strips * (cd.M / H);
     int grid = (per_sm * gf_sm_count() + div - 1) / div;
@@ -558,7 +717,8 @@ cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int var_mode, i
 
 cudaError_t configure_gf_kernel() {
   const int bytes = (int)(GFW_WARPS * gfw_ring_floats(GF_RMAX) * sizeof(float));
-  const GfKernel ks[6] = {k_guided_filter<SumDF, false>,  k_guided_filter<SumDF, true>,
+  const GfKernel ks[8] = {k_guided_filter<SumIG, false>,  k_guided_filter<SumIG, true>,
+                          k_guided_filter<SumDF, false>,  k_guided_filter<SumDF, true>,
                           k_guided_filter<SumF64, false>, k_guided_filter<SumF64, true>,
                           k_guided_filter<SumF32, false>, k_guided_filter<SumF32, true>};
   for (GfKernel k : ks) {

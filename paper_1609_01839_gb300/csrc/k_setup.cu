@@ -184,6 +184,47 @@ __global__ void k_unpack_dc(ClassDesc cd, const ImgDesc* __restrict__ imgs, cons
   }
 }
 
+// y (m x n) -> canvas (M x N): symmetric reflection at the bottom and right
+// edges with period 2m (2n), the edge sample repeated.
+__global__ void k_pad_symmetric(const float* __restrict__ y, int m, int n, float* __restrict__ dst,
+                                int M, int N) {
+  const size_t total = (size_t)M * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx - (size_t)i * N);
+    const int ti = i % (2 * m), tj = j % (2 * n);
+    const int si = ti < m ? ti : 2 * m - 1 - ti, sj = tj < n ? tj : 2 * n - 1 - tj;
+    dst[idx] = __ldg(&y[(size_t)si * n + sj]);
+  }
+}
+
+// canvas (M x N) -> its top-left m x n part.
+__global__ void k_crop(const float* __restrict__ src, int N, float* __restrict__ dst, int m, int n) {
+  const size_t total = (size_t)m * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx - (size_t)i * n);
+    dst[idx] = __ldg(&src[(size_t)i * N + j]);
+  }
+}
+
+static unsigned plane_blocks(size_t total) {
+  size_t nb = (total + 255) / 256;
+  if (nb > 152 * 16) nb = 152 * 16;
+  return (unsigned)(nb < 1 ? 1 : nb);
+}
+
+cudaError_t launch_pad_symmetric(const float* y, int m, int n, float* dst, int M, int N,
+                                 cudaStream_t s) {
+  k_pad_symmetric<<<plane_blocks((size_t)M * N), 256, 0, s>>>(y, m, n, dst, M, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crop(const float* src, int N, float* dst, int m, int n, cudaStream_t s) {
+  k_crop<<<plane_blocks((size_t)m * n), 256, 0, s>>>(src, N, dst, m, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
   const size_t P = (size_t)c.cd.M * c.cd.N;
   int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));
@@ -225,12 +266,14 @@ cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s) {
 
 cudaError_t configure_fft_kernels();
 cudaError_t configure_gf_kernel();
+cudaError_t configure_gfc_kernels();
 cudaError_t configure_df_kernels();
 
 cudaError_t configure_kernels() {
   cudaError_t e = configure_fft_kernels();
   if (e != cudaSuccess) return e;
   if ((e = configure_df_kernels()) != cudaSuccess) return e;
+  if ((e = configure_gfc_kernels()) != cudaSuccess) return e;
   return configure_gf_kernel();
 }
 

@@ -18,14 +18,12 @@ enum PlaneSel : int {
   SEL_UP = 8,  // u_p (real)
 };
 
-// Tile shapes of the pass kernels (threads per block, which fixes rows per
-// row item and columns per column item); set by the autotuner.
-struct TileConfig {
-  int row_threads = 256;
-  int col_threads = 256;
-  int solve_threads = 256;
-};
-extern TileConfig g_tiles;
+// Tile shapes of one size class (threads per block of the row passes, which
+// fixes rows per row item; of the column passes, which fixes the spectra's
+// tile width; rows per guided-filter item), chosen by gfdeconv_autotune.
+constexpr int DEF_ROW_THREADS = 256;
+constexpr int DEF_COL_THREADS = 256;
+constexpr int DEF_GF_ROWS = 64;
 
 struct Tables {
   const float2* tw;    // W_L^m for every L = 2..4096, size L at offset tab_off(L)
@@ -47,6 +45,9 @@ struct ClassLaunch {
   int n_rad_groups;
   RadGroup rad_groups[9];
   int grid_div;         // persistent grids use 1/grid_div of the resident slots (0 = 1)
+  int row_threads;      // threads per row-pass block (0 = DEF_ROW_THREADS)
+  int gf_rows;          // largest rows per guided-filter item (0 = DEF_GF_ROWS)
+  int class_id;         // index of the class in its plan (instrumentation)
 };
 
 // Row pass of the 2-D real DFT: real plane src -> packed rows dst.
@@ -57,8 +58,11 @@ cudaError_t launch_row_r2c(const ClassLaunch& c, const Tables& t, int src, int d
 // unless sel1 < 0), outputs scaled by `scale`.
 cudaError_t launch_row_c2r(const ClassLaunch& c, const Tables& t, int sel0, int sel1, int dsel0,
                            int dsel1, float scale, cudaStream_t s);
-// Tile width (columns per tile) of the spectra of an M x N class.
-int class_tile_width(int M, int N);
+// Tile width (columns per tile) of the spectra of an M x N class whose
+// column passes run col_threads threads per block (0 = default).
+int class_tile_width(int M, int N, int col_threads);
+// Rows per item of a row pass of length-L transforms on an M-row class.
+int rows_per_item(int L, int M, int row_threads);
 // Plain column FFT src -> dst (in place allowed), forward or inverse.
 cudaError_t launch_col_plain(const ClassLaunch& c, const Tables& t, int src, int dst,
                              bool inverse, cudaStream_t s);
@@ -74,6 +78,14 @@ cudaError_t launch_col_solve_inv(const ClassLaunch& c, const Tables& t, cudaStre
 // var_mode: GFD_VAR_*; boundary: GFD_BOUNDARY_*.
 cudaError_t launch_guided_filter(const ClassLaunch& c, int iter, int var_mode, int boundary,
                                  cudaStream_t s);
+// Colour guided filter: guidance I planar [3][M][N], p, window w; ab is a
+// 4 * M * N workspace (a_r, a_g, a_b, b); u the output.
+cudaError_t launch_guided_filter_color(const float* I, const float* p, int M, int N, int w,
+                                       double eps, int boundary, float* ab, float* u,
+                                       cudaStream_t s);
+// Largest |u_I|, |u_p| of every image into ImgState::absmax (which must be
+// zero before), for guided-filter calls outside a solve.
+cudaError_t launch_plane_absmax(const ClassLaunch& c, cudaStream_t s);
 // Double-float 2-D real DFT of real plane src into spectrum plane dst
 // (SEL_H or SEL_YS); uses the S and Q_I planes as scratch.
 cudaError_t launch_fft2_r2c_df(const ClassLaunch& c, const float4* twdf, int src, int dst,
@@ -84,6 +96,11 @@ cudaError_t launch_init_u(const ClassLaunch& c, cudaStream_t s);
 cudaError_t launch_setup_init(const ClassLaunch& c, double rho_fixed, cudaStream_t s);
 cudaError_t launch_embed_psf(const ClassLaunch& c, int dst, cudaStream_t s);
 cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s);
+
+// Symmetric padding of an m x n plane to M x N, and the top-left crop back.
+cudaError_t launch_pad_symmetric(const float* y, int m, int n, float* dst, int M, int N,
+                                 cudaStream_t s);
+cudaError_t launch_crop(const float* src, int N, float* dst, int m, int n, cudaStream_t s);
 
 // Opt every kernel into large dynamic shared memory (once per process/device).
 cudaError_t configure_kernels();
