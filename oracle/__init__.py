@@ -20,3 +20,4 @@ from .gfdeconv import (  # noqa: F401
     guided_filter_color, pad_symmetric, crop,
     isnr, iterate, solve, NONCONVERGED, LAMBDA_LO, LAMBDA_RTOL,
 )
+from . import adjoint  # noqa: F401  (gradient of the unrolled method, oracle/adjoint.py)
