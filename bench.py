@@ -402,7 +402,14 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    probs = generate(shard_indices(rank, world, args.images))  # before any CUDA work
+    iters = ITERS
+    if args.workload == "large":  # profiler runs only: the 4 x 4096^2 batch
+        with mp.get_context("spawn").Pool(C4_BATCH) as pool:
+            probs = pool.map(_gen_c4, range(C4_BATCH))
+        iters = args.iters or C4_ITERS
+    else:
+        probs = generate(shard_indices(rank, world, args.images))  # before any CUDA work
+        iters = args.iters or ITERS
     import paper_1609_01839_gb300 as gfd
 
     true_px = sum(p.true_shape[0] * p.true_shape[1] for p in probs)
@@ -410,19 +417,28 @@ def run_ours(args):
     items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
               "sigma": p.sigma, "w": p.w, "eps": p.eps,
               "u_orig": torch.from_numpy(p.u_orig).to(dev)} for p in probs]
-    ctx_var = gfd.VAR_COMPENSATED  # double-float window sums (FP64-equivalent variance)
-    ctx = gfd.Context(local, var_precision=ctx_var)
-    arr = ctx.make_images(items, ITERS)
+    ctx_var = gfd.VAR_COMPENSATED  # split window sums (exact leading parts)
+    ctx = gfd.Context(local, var_precision=ctx_var, tune_cache=args.tune_file)
+    arr = ctx.make_images(items, iters)
     stream = torch.cuda.current_stream(dev)
     # tile shapes from the autotuner, measured on this workload (untimed)
     t0 = time.perf_counter()
     tune_dir = os.environ.get("GFD_ARTIFACT_DIR", os.path.join(ROOT, "artifacts"))
     os.makedirs(tune_dir, exist_ok=True)
     tune_path = os.path.join(tune_dir, f"tune_rank{rank}.txt")
-    if args.no_tune:
+    if args.no_tune or args.tune_file:
         tuned = None
+        if args.tune_file:
+            tune_path = args.tune_file
+            tuned = {"file": os.path.basename(args.tune_file), "chains": None, "classes": {}}
+            for p in probs:
+                M, N = p.shape
+                col, row, gfr, ch = ctx.tune_get(M, N)
+                tuned["chains"] = ch
+                tuned["classes"][f"{M}x{N}"] = {"col_threads": col, "row_threads": row,
+                                                "gf_rows": gfr}
     else:
-        ctx.autotune(arr, ITERS, tune_path, stream)
+        ctx.autotune(arr, iters, tune_path, stream)
         tuned = {"seconds": round(time.perf_counter() - t0, 2), "chains": None, "classes": {}}
         for p in probs:
             M, N = p.shape
@@ -430,7 +446,7 @@ def run_ours(args):
             tuned["chains"] = ch
             tuned["classes"][f"{M}x{N}"] = {"col_threads": col, "row_threads": row, "gf_rows": gfr}
     for _ in range(max(args.warmup, 1)):  # the first call also builds and captures the graph
-        ctx.solve_batched_images(arr, ITERS, stream)
+        ctx.solve_batched_images(arr, iters, stream)
     torch.cuda.synchronize(dev)
     launches_per_step = ctx.last_launch_count()
     st = ctx.status(len(items))
@@ -444,7 +460,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         ev0.record(stream)
         for _ in range(args.steps):
-            ctx.solve_batched_images(arr, ITERS, stream)
+            ctx.solve_batched_images(arr, iters, stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         if dist is not None:
@@ -453,8 +469,8 @@ def run_ours(args):
     ms_max = reduce_max(ms, dist, dev)
     total_true = reduce_sum(float(true_px), dist, dev)
     total_canvas = reduce_sum(float(canvas_px), dist, dev)
-    value = total_true * ITERS * args.steps / (ms_max / 1e3) / 1e6
-    value_canvas = total_canvas * ITERS * args.steps / (ms_max / 1e3) / 1e6
+    value = total_true * iters * args.steps / (ms_max / 1e3) / 1e6
+    value_canvas = total_canvas * iters * args.steps / (ms_max / 1e3) / 1e6
     if args.only_solve:  # lean mode for profilers: the timed solves only
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -597,11 +613,20 @@ def main(argv=None):
                     help="time the batched solves only (for profiler runs)")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the built-in tile shapes instead of the autotuner's")
+    ap.add_argument("--tune-file", default=None,
+                    help="read tile shapes from this file (written by an earlier run) "
+                         "instead of tuning")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4 x 4096^2 bandwidth-stress leg")
     ap.add_argument("--table1", action="store_true",
                     help="run the Table 1 settings sweep instead of the benchmark")
+    ap.add_argument("--workload", choices=["batch", "large"], default="batch",
+                    help="with --only-solve: the 256-image batch or the 4 x 4096^2 batch")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="with --only-solve: iterations per solve (0 = the workload's)")
     args = ap.parse_args(argv)
+    if (args.workload != "batch" or args.iters) and not args.only_solve:
+        ap.error("--workload / --iters are profiler options: use them with --only-solve")
     if args.table1:
         return run_table1(args)
     if args.impl == "reference":
