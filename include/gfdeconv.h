@@ -121,7 +121,18 @@ typedef struct {
   const float* u_init; /* starting u_E (resume), M*N, or NULL for Step 0's 0 */
   float* uI_out;    /* last iteration's u_I (Eq. 8), M*N, or NULL */
   float* up_out;    /* last iteration's u_p (Eq. 9), M*N, or NULL */
+  float* u_iters;   /* [iters][M*N] checkpoints: the iterate u_E^k entering each
+                       iteration k (u_E^0 = 0 or u_init), for gfdeconv_backward_batched;
+                       or NULL */
 } gfdeconv_image;
+
+/* Gradients of one image for gfdeconv_backward_batched (device pointers). */
+typedef struct {
+  const float* g_u; /* in: dL/du^K, M*N (u^K = the solve's u_out) */
+  float* g_y;       /* out: dL/dy, M*N */
+  float* g_h;       /* out: dL/dh, kh*kw */
+  double* g_eps;    /* out: dL/deps, one double */
+} gfdeconv_grad;
 
 /* Create a context on `cuda_device` (opts NULL = defaults).  Allocates the
  * twiddle and gradient-weight tables; workspaces grow on first use. */
@@ -278,6 +289,23 @@ int gfdeconv_tune_read(const char* path, int* chains, int* n_classes, int* shape
  * its chain count; any output pointer may be NULL. */
 int gfdeconv_tune_get(gfdeconv_ctx* ctx, int M, int N, int* col_threads, int* row_threads,
                       int* gf_rows, int* chains);
+
+/* Reverse mode of the unrolled method: given dL/du^K for each image, the
+ * gradients dL/dy, dL/dh and dL/deps of a loss L of the result u^K of
+ * `iters` iterations (Sec. 3.1 Steps 0-3 with Sec. 3.2's lambda).  `imgs`
+ * are the descriptors of a gfdeconv_solve_batched call with u_iters set (its
+ * checkpoints are read, nothing else of its outputs); all images share one
+ * canvas size, windows are periodic (gfdeconv_opts.boundary = 0).  Each
+ * iteration is recomputed from its checkpoint and undone in reverse: the
+ * guided filter (Eq. 3-5), the spectral solves (Eq. 8-9), lambda through the
+ * implicit derivative of Eq. 11 (where lambda = inf, u_E in K, lambda is a
+ * constant and u_I = u_p = u_E), the DFTs; H, Y and T = rho P sigma^2
+ * (Eq. 12) collect their gradients over the iterations.  FP32 spectra and
+ * planes, FP64 window sums and reductions.  The context's cached solve plan is
+ * replaced.  Returns GFD_ERR_INVALID_ARG for missing checkpoints or mixed
+ * canvas sizes. */
+int gfdeconv_backward_batched(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
+                              const gfdeconv_grad* grads, int iters, void* stream);
 
 /* Number of kernel launches the last solve issued (for instrumentation). */
 long long gfdeconv_last_launch_count(gfdeconv_ctx* ctx);

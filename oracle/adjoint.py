@@ -102,10 +102,10 @@ def _rho_parts(y, h, sigma):
             "rho": min(1.0, math.sqrt(rad)), "clamped": math.sqrt(rad) >= 1.0}
 
 
-def solve_with_grad(y, h, sigma, w, eps, iters, u_clean):
-    """L = mean((u^K - u_clean)^2) after `iters` iterations from u_E = 0 and
-    its gradient.  Returns a dict: loss, g_h (kh x kw), g_eps, g_y (M x N),
-    lam (the forward lambdas), u (u^K)."""
+def solve_with_grad(y, h, sigma, w, eps, iters, u_clean, u_init=None):
+    """L = mean((u^K - u_clean)^2) after `iters` iterations from u_E = 0 (or
+    the constant start u_init) and its gradient.  Returns a dict: loss, g_h
+    (kh x kw), g_eps, g_y (M x N), lam (the forward lambdas), u (u^K)."""
     y = np.asarray(y, dtype=np.float64)
     h = np.asarray(h, dtype=np.float64)
     u_clean = np.asarray(u_clean, dtype=np.float64)
@@ -118,7 +118,7 @@ def solve_with_grad(y, h, sigma, w, eps, iters, u_clean):
     T = rp["rho"] * P * sigma * sigma
     # forward, keeping the checkpoints u_E^k
     checkpoints, lams = [], []
-    uE = np.zeros((M, N))
+    uE = np.zeros((M, N)) if u_init is None else np.asarray(u_init, dtype=np.float64)
     for _ in range(iters):
         checkpoints.append(uE)
         st = _forward_step(H, Y, D2, uE, T, w, eps)
@@ -189,8 +189,8 @@ def solve_with_grad(y, h, sigma, w, eps, iters, u_clean):
     return {"loss": loss, "g_h": g_h, "g_eps": g_eps, "g_y": g_y, "lam": lams, "u": u}
 
 
-def loss_only(y, h, sigma, w, eps, iters, u_clean):
+def loss_only(y, h, sigma, w, eps, iters, u_clean, u_init=None):
     """L = mean((u^K - u_clean)^2) of the oracle's solve (for finite differences)."""
     r = G.solve(np.asarray(y, dtype=np.float64), np.asarray(h, dtype=np.float64), sigma, w, eps,
-                iters)
+                iters, u_init=u_init)
     return float(np.mean((r["u"] - np.asarray(u_clean, dtype=np.float64)) ** 2))

@@ -74,7 +74,14 @@ class Image(ctypes.Structure):
         ("isnr_out", ctypes.c_void_p), ("res_out", ctypes.c_void_p),
         ("u_orig", ctypes.c_void_p), ("u_init", ctypes.c_void_p),
         ("uI_out", ctypes.c_void_p), ("up_out", ctypes.c_void_p),
+        ("u_iters", ctypes.c_void_p),
     ]
+
+
+class Grad(ctypes.Structure):
+    """Mirror of gfdeconv_grad."""
+    _fields_ = [("g_u", ctypes.c_void_p), ("g_y", ctypes.c_void_p), ("g_h", ctypes.c_void_p),
+                ("g_eps", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):
@@ -113,6 +120,8 @@ def _load():
         "gfdeconv_last_cuda_error": (ctypes.c_char_p, []),
         "gfdeconv_device_arch": (ci, [ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]),
         "gfdeconv_autotune": (ci, [vp, ci, ctypes.POINTER(Image), ci, ctypes.c_char_p, vp]),
+        "gfdeconv_backward_batched": (ci, [vp, ci, ctypes.POINTER(Image), ctypes.POINTER(Grad), ci,
+                                           vp]),
         "gfdeconv_tune_read": (ci, [ctypes.c_char_p, ctypes.POINTER(ci), ctypes.POINTER(ci),
                                     ctypes.POINTER(ci), ci]),
         "gfdeconv_tune_get": (ci, [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci),
@@ -247,10 +256,11 @@ class Context:
             raise GfdError(rc, "gfdeconv_solve")
         return u, lam, isnr
 
-    def make_images(self, items, iters, want_res=False, want_uIp=False):
+    def make_images(self, items, iters, want_res=False, want_uIp=False, want_checkpoints=False):
         """Descriptors for solve_batched from dicts with CUDA tensors
         y, h, sigma, w, eps and optional u_orig, u_init.  Allocates u (and
-        lambda / isnr / res / u_I / u_p) and stores them in each dict."""
+        lambda / isnr / res / u_I / u_p / the per-iteration checkpoints
+        u_iters) and stores them in each dict."""
         import torch
         arr = (Image * len(items))()
         for i, it in enumerate(items):
@@ -265,6 +275,8 @@ class Context:
             if want_uIp:
                 it["uI"] = torch.empty((M, N), dtype=torch.float32, device=dev)
                 it["up"] = torch.empty((M, N), dtype=torch.float32, device=dev)
+            if want_checkpoints:
+                it["u_iters"] = torch.empty((max(iters, 1), M, N), dtype=torch.float32, device=dev)
             a = arr[i]
             a.y = _ptr(y, "y", torch.float32)
             a.M, a.N = M, N
@@ -281,6 +293,7 @@ class Context:
             a.u_init = _ptr(it.get("u_init"), "u_init", torch.float32, M * N)
             a.uI_out = _ptr(it.get("uI"), "uI", torch.float32, M * N)
             a.up_out = _ptr(it.get("up"), "up", torch.float32, M * N)
+            a.u_iters = _ptr(it.get("u_iters"), "u_iters", torch.float32)
         return arr
 
     def solve_batched_images(self, arr, iters, stream=None):
@@ -288,11 +301,53 @@ class Context:
         if rc != 0:
             raise GfdError(rc, "gfdeconv_solve_batched")
 
-    def solve_batched(self, items, iters, stream=None, want_res=False, want_uIp=False):
+    def solve_batched(self, items, iters, stream=None, want_res=False, want_uIp=False,
+                      want_checkpoints=False):
         """Batched solve of dicts (see make_images); results land in the dicts."""
-        arr = self.make_images(items, iters, want_res, want_uIp)
+        arr = self.make_images(items, iters, want_res, want_uIp, want_checkpoints)
         self.solve_batched_images(arr, iters, stream)
         return items
+
+    def backward_batched(self, items, iters, g_us, stream=None):
+        """gfdeconv_backward_batched: items are the dicts of a solve_batched
+        call made with want_checkpoints=True, g_us the gradients dL/du of their
+        results.  Returns [(g_y, g_h, g_eps)] (CUDA tensors; g_eps float64)."""
+        import torch
+        arr = (Image * len(items))()
+        grads = (Grad * len(items))()
+        out = []
+        for i, (it, gu) in enumerate(zip(items, g_us)):
+            y, h = it["y"], it["h"]
+            M, N = y.shape
+            a = arr[i]
+            a.y = _ptr(y, "y", torch.float32)
+            a.M, a.N = M, N
+            a.h = _ptr(h, "h", torch.float32)
+            a.kh, a.kw = h.shape
+            a.sigma, a.w, a.eps = float(it["sigma"]), int(it["w"]), float(it["eps"])
+            a.u_out = _ptr(it["u"], "u", torch.float32, M * N)
+            a.u_iters = _ptr(it["u_iters"], "u_iters", torch.float32)
+            gy = torch.empty_like(y)
+            gh = torch.empty_like(h)
+            ge = torch.empty((), dtype=torch.float64, device=y.device)
+            g = grads[i]
+            g.g_u = _ptr(gu, "g_u", torch.float32, M * N)
+            g.g_y, g.g_h, g.g_eps = gy.data_ptr(), gh.data_ptr(), ge.data_ptr()
+            out.append((gy, gh, ge))
+        rc = _lib.gfdeconv_backward_batched(self._h, len(items), arr, grads, int(iters),
+                                            _stream(stream))
+        if rc != 0:
+            raise GfdError(rc, "gfdeconv_backward_batched")
+        return out
+
+    def deconv(self, y, h, eps, sigma, w, iters, stream=None):
+        """Differentiable solve: u^iters of a batch (y: (B, M, N) or (M, N);
+        h: (B, kh, kw) or (kh, kw); eps: a tensor of B values or one value;
+        sigma: a float or B floats; w one odd window).  Gradients with respect
+        to y, h and eps come from gfdeconv_backward_batched (the library's
+        hand-written adjoint), through torch.autograd."""
+        return _Deconv.apply(y, h, eps, self, sigma, int(w), int(iters), stream)
+
 
     def make_host_images(self, items, iters):
         """Descriptors for solve_batched_host from dicts of pinned CPU tensors
@@ -452,3 +507,59 @@ class Context:
 
     def last_launch_count(self) -> int:
         return int(_lib.gfdeconv_last_launch_count(self._h))
+
+
+def _autograd_function():
+    import torch
+
+    class Deconv(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, y, h, eps, lib, sigma, w, iters, stream):
+            single = y.dim() == 2
+            Y = y.detach().reshape((-1,) + tuple(y.shape[-2:])).contiguous().float()
+            Hh = h.detach().reshape((-1,) + tuple(h.shape[-2:])).contiguous().float()
+            B = Y.shape[0]
+            if Hh.shape[0] == 1 and B > 1:
+                Hh = Hh.expand(B, -1, -1).contiguous()
+            E = torch.as_tensor(eps, dtype=torch.float64).reshape(-1)
+            if E.numel() == 1 and B > 1:
+                E = E.expand(B)
+            sig = [float(sigma)] * B if not hasattr(sigma, "__len__") else [float(s) for s in sigma]
+            items = [{"y": Y[b], "h": Hh[b], "sigma": sig[b], "w": w, "eps": float(E[b])}
+                     for b in range(B)]
+            lib.solve_batched(items, iters, stream=stream, want_checkpoints=True)
+            fctx.lib, fctx.items, fctx.iters, fctx.stream = lib, items, iters, stream
+            fctx.shapes = (y.shape, h.shape, torch.as_tensor(eps).shape, single, Hh.shape[0] != h.reshape((-1,) + tuple(h.shape[-2:])).shape[0])
+            fctx.eps_dtype = torch.as_tensor(eps).dtype
+            u = torch.stack([it["u"] for it in items])
+            return u[0] if single else u
+
+        @staticmethod
+        def backward(fctx, g_u):
+            import torch as T
+            G = g_u.reshape((-1,) + tuple(g_u.shape[-2:])).contiguous().float()
+            res = fctx.lib.backward_batched(fctx.items, fctx.iters, [G[b] for b in range(G.shape[0])],
+                                            fctx.stream)
+            y_shape, h_shape, e_shape, single, h_expanded = fctx.shapes
+            gy = T.stack([r[0] for r in res]).reshape(y_shape)
+            gh = T.stack([r[1] for r in res])
+            gh = gh.sum(0) if h_expanded else gh
+            gh = gh.reshape(h_shape)
+            ge = T.stack([r[2] for r in res])
+            ge = (ge.sum() if len(e_shape) == 0 or T.Size(e_shape).numel() == 1 else ge).reshape(e_shape)
+            return gy, gh, ge.to(fctx.eps_dtype), None, None, None, None, None
+
+    return Deconv
+
+
+class _LazyDeconv:
+    fn = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls.fn is None:
+            cls.fn = _autograd_function()
+        return cls.fn.apply(*args)
+
+
+_Deconv = _LazyDeconv

@@ -52,6 +52,7 @@ struct Plan {
   // share the SMs (a kernel's tail overlaps the next kernel of another chain)
   std::vector<ClassLaunch> parts[CHAINS];
   int nparts = CHAINS;
+  bool checkpoints = false;  // some image keeps its iterates (u_iters)
   std::vector<ImgDesc> h_imgs;           // internal order
   std::vector<gfdeconv_image> user;      // internal order
   cudaGraphExec_t exec = nullptr;
@@ -152,6 +153,8 @@ struct gfdeconv_ctx {
   char* hstage = nullptr;  // pinned host staging of the small per-image arrays
   size_t hstage_bytes = 0;
   TuneTable tune;          // tile shapes per canvas size
+  char* adj_ws = nullptr;  // workspace of gfdeconv_backward_batched
+  size_t adj_ws_bytes = 0;
 };
 
 namespace {
@@ -172,7 +175,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 // Device image planes are read and written with 16-byte accesses.
 int validate_device_planes(const gfdeconv_image& im) {
   if (!aligned16(im.y) || !aligned16(im.u_out) || !aligned16(im.u_orig) || !aligned16(im.u_init) ||
-      !aligned16(im.uI_out) || !aligned16(im.up_out))
+      !aligned16(im.uI_out) || !aligned16(im.up_out) || !aligned16(im.u_iters))
     return GFD_ERR_INVALID_ARG;
   return GFD_OK;
 }
@@ -314,6 +317,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
       d.u = im.u_out;
       d.uo = im.u_orig;
       d.u0 = im.u_init;
+      d.u_iters = im.u_iters;
       d.lam_out = im.lambda_out;
       d.isnr_out = im.isnr_out;
       d.res_out = im.res_out;
@@ -344,6 +348,7 @@ cudaError_t build_plan(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int i
       d.rowsum = reinterpret_cast<double*>(cur);
       cur += align256((size_t)im.M * sizeof(double));
       cl.max_rad = std::max(cl.max_rad, (im.w - 1) / 2);
+      if (im.u_iters) pl.checkpoints = true;
       pl.order.push_back(ui);
       pl.h_imgs.push_back(d);
       pl.user.push_back(im);
@@ -446,6 +451,10 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
     for (int k = 0; k < pl.iters; ++k) {
       for (auto& cl : classes) {
         if (tm) tm->cur_cls = cl.class_id;
+        if (pl.checkpoints) {  // u_E^k of the images that keep checkpoints
+          GFD_T(GFD_PHASE_COPY, launch_save_iterate(cl, k, s));
+          ++L;
+        }
         GFD_T(GFD_PHASE_ROW_FWD, launch_row_r2c(cl, t, SEL_U, SEL_S, true, s));
         GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
         L += 2;
@@ -791,6 +800,7 @@ void gfdeconv_destroy(gfdeconv_ctx* c) {
   if (c->d_st) cudaFree(c->d_st);
   if (c->aux_st) cudaFree(c->aux_st);
   if (c->stage) cudaFree(c->stage);
+  if (c->adj_ws) cudaFree(c->adj_ws);
   if (c->hstage) cudaFreeHost(c->hstage);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (int q = 0; q < CHAINS - 1; ++q) {
@@ -1012,6 +1022,217 @@ int gfdeconv_solve_batched_timed(gfdeconv_ctx* c, int n, const gfdeconv_image* i
   return GFD_OK;
 }
 
+int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs,
+                              const gfdeconv_grad* grads, int iters, void* stream) {
+  if (!c || !imgs || !grads || n <= 0 || iters < 1) return GFD_ERR_INVALID_ARG;
+  if (c->opts.boundary != GFD_BOUNDARY_PERIODIC) return GFD_ERR_INVALID_ARG;
+  const int M = imgs[0].M, N = imgs[0].N;
+  int max_psf = 1;
+  for (int i = 0; i < n; ++i) {
+    int r = validate_image(imgs[i], iters);
+    if (r == GFD_OK) r = validate_device_planes(imgs[i]);
+    if (r != GFD_OK) return r;
+    if (imgs[i].M != M || imgs[i].N != N || !imgs[i].u_iters) return GFD_ERR_INVALID_ARG;
+    const gfdeconv_grad& g = grads[i];
+    if (!g.g_u || !g.g_y || !g.g_h || !g.g_eps || !aligned16(g.g_u) || !aligned16(g.g_y))
+      return GFD_ERR_INVALID_ARG;
+    max_psf = std::max(max_psf, imgs[i].kh * imgs[i].kw);
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)M * N;
+  // per image: 18 real planes (16 of the adjoint, u_E^k, the recomputed u) and
+  // 11 spectra (10 of the adjoint, the FFT scratch) of P floats each, 12
+  // doubles (lambda, g_eps, the sums)
+  const int n_real = 18, n_spec = 11, n_dbl = 12;
+  const size_t plane = align256(P * sizeof(float));
+  const size_t per_img = (n_real + n_spec) * plane + align256(n_dbl * sizeof(double));
+  const size_t descs_bytes = align256(sizeof(AdjDesc) * n);
+  const int n_fft = 11;  // ImgDesc arrays of the DFTs below
+  const size_t fft_bytes = align256(sizeof(ImgDesc) * n) * n_fft;
+  const size_t need = per_img * n + descs_bytes + fft_bytes;
+  cudaError_t e;
+  if (need > c->adj_ws_bytes) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return map_err(e);
+    if (c->adj_ws) cudaFree(c->adj_ws);
+    c->adj_ws = nullptr;
+    c->adj_ws_bytes = 0;
+    if ((e = cudaMalloc(&c->adj_ws, need)) != cudaSuccess) return map_err(e);
+    c->adj_ws_bytes = need;
+  }
+  char* cur = c->adj_ws;
+  AdjDesc* d_desc = reinterpret_cast<AdjDesc*>(cur);
+  cur += descs_bytes;
+  ImgDesc* d_fft = reinterpret_cast<ImgDesc*>(cur);
+  const size_t fft_stride = align256(sizeof(ImgDesc) * n) / sizeof(ImgDesc);
+  cur += fft_bytes;
+  std::vector<AdjDesc> ad(n);
+  std::vector<float*> uEcur(n), ucur(n), hc(n), scratch(n);
+  std::vector<std::vector<ImgDesc>> fd(n_fft, std::vector<ImgDesc>(n));
+  std::vector<gfdeconv_image> rec(imgs, imgs + n);  // the recomputed forward steps
+  for (int i = 0; i < n; ++i) {
+    char* b = cur + per_img * i;
+    auto realp = [&](int k) { return reinterpret_cast<float*>(b + plane * k); };
+    auto specp = [&](int k) { return reinterpret_cast<float2*>(b + plane * (n_real + k)); };
+    double* dbl = reinterpret_cast<double*>(b + plane * (n_real + n_spec));
+    AdjDesc& a = ad[i];
+    a = AdjDesc{};
+    a.y = imgs[i].y;
+    a.h = imgs[i].h;
+    a.kh = imgs[i].kh;
+    a.kw = imgs[i].kw;
+    a.sigma = imgs[i].sigma;
+    a.eps = imgs[i].eps;
+    a.rho_fixed = c->opts.rho;
+    float* uIp = realp(0);
+    float* upp = realp(1);
+    a.uI = uIp;
+    a.up = upp;
+    a.gu = realp(2);
+    a.A = realp(3);
+    a.MU = realp(4);
+    a.PB = realp(5);
+    a.VE = realp(6);
+    a.GI0 = realp(7);
+    a.GCOV = realp(8);
+    a.GVAR = realp(9);
+    a.GMU = realp(10);
+    a.GPB = realp(11);
+    a.guI = realp(12);
+    a.gup = realp(13);
+    a.gtmp = realp(14);
+    a.gtmp2 = realp(15);
+    uEcur[i] = realp(16);
+    ucur[i] = realp(17);
+    a.H = specp(0);
+    a.Y = specp(1);
+    a.UE = specp(2);
+    a.UI = specp(3);
+    a.Up = specp(4);
+    a.GUI = specp(5);
+    a.GUp = specp(6);
+    a.gUE = specp(7);
+    a.gH = specp(8);
+    a.gY = specp(9);
+    scratch[i] = reinterpret_cast<float*>(specp(10));
+    hc[i] = a.gtmp2;  // the embedded PSF, transformed before gtmp2 is needed
+    a.lam = dbl;
+    a.g_eps = dbl + 1;
+    a.acc = dbl + 2;  // ADJ_ACC (9) doubles
+    a.g_eps_out = grads[i].g_eps;
+    a.gy_out = grads[i].g_y;
+    a.gh_out = grads[i].g_h;
+    // the forward step recomputed from u_E^k (copied into uEcur each step)
+    gfdeconv_image& r = rec[i];
+    r.u_init = uEcur[i];
+    r.u_out = ucur[i];
+    r.uI_out = uIp;
+    r.up_out = upp;
+    r.lambda_out = dbl;
+    r.isnr_out = nullptr;
+    r.res_out = nullptr;
+    r.u_orig = nullptr;
+    r.u_iters = nullptr;
+    // DFT descriptors: r2c(src -> dst) uses u, S, Y; c2r(src -> dst) uses QI, uI
+    auto r2c = [&](int op, const float* src, float2* dst) {
+      ImgDesc& q = fd[op][i];
+      q = ImgDesc{};
+      q.u = const_cast<float*>(src);
+      q.S = reinterpret_cast<float2*>(scratch[i]);
+      q.Y = dst;
+    };
+    auto c2r = [&](int op, float2* src, float* dst) {
+      ImgDesc& q = fd[op][i];
+      q = ImgDesc{};
+      q.QI = src;
+      q.uI = dst;
+    };
+    r2c(0, uEcur[i], a.UE);
+    r2c(1, uIp, a.UI);
+    r2c(2, upp, a.Up);
+    r2c(3, a.guI, a.GUI);
+    r2c(4, a.gup, a.GUp);
+    r2c(5, hc[i], a.H);
+    r2c(6, imgs[i].y, a.Y);
+    c2r(7, a.gUE, a.gtmp);
+    c2r(8, a.gY, a.gtmp);
+    c2r(9, a.gH, a.gtmp2);
+    ImgDesc& q = fd[10][i];  // the PSF embedding writes q.uI
+    q = ImgDesc{};
+    q.h = imgs[i].h;
+    q.kh = imgs[i].kh;
+    q.kw = imgs[i].kw;
+    q.uI = hc[i];
+  }
+  if ((e = cudaMemcpyAsync(d_desc, ad.data(), sizeof(AdjDesc) * n, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return map_err(e);
+  for (int op = 0; op < n_fft; ++op)
+    if ((e = cudaMemcpyAsync(d_fft + fft_stride * op, fd[op].data(), sizeof(ImgDesc) * n,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return map_err(e);
+  const Tables t{c->tw, c->d2, c->twdf};
+  auto cls = [&](int op) {
+    ClassLaunch cl{};
+    cl.cd = ClassDesc{M, N, n, 0, N / 2};
+    cl.imgs = d_fft + fft_stride * op;
+    cl.st = nullptr;
+    return cl;
+  };
+  auto fwd = [&](int op) -> cudaError_t {
+    const ClassLaunch cl = cls(op);
+    cudaError_t r = launch_row_r2c(cl, t, SEL_U, SEL_S, false, s);
+    if (r == cudaSuccess) r = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s);
+    return r;
+  };
+  auto adj = [&](int op) -> cudaError_t {  // F^H of a packed Hermitian spectrum (scale 1)
+    const ClassLaunch cl = cls(op);
+    cudaError_t r = launch_col_plain(cl, t, SEL_QI, SEL_QI, true, s);
+    if (r == cudaSuccess) r = launch_row_c2r(cl, t, SEL_QI, -1, SEL_UI, -1, 1.0f, s);
+    return r;
+  };
+#define GFD_ADJ_CK(x)                    \
+  do {                                   \
+    if ((e = (x)) != cudaSuccess) return map_err(e); \
+  } while (0)
+  // setup: H, Y, the sums of Eq. 12; zeroed accumulators; g_u of u^K
+  for (int i = 0; i < n; ++i) {
+    GFD_ADJ_CK(cudaMemsetAsync(ad[i].gH, 0, P * sizeof(float), s));
+    GFD_ADJ_CK(cudaMemsetAsync(ad[i].gY, 0, P * sizeof(float), s));
+    GFD_ADJ_CK(cudaMemsetAsync(const_cast<double*>(ad[i].lam), 0, n_dbl * sizeof(double), s));
+    GFD_ADJ_CK(cudaMemcpyAsync(ad[i].gu, grads[i].g_u, P * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s));
+  }
+  GFD_ADJ_CK(launch_embed_psf(cls(10), SEL_UI, s));
+  GFD_ADJ_CK(fwd(5));
+  GFD_ADJ_CK(fwd(6));
+  GFD_ADJ_CK(launch_adj_stats(d_desc, n, M, N, s));
+  // the steps, last first
+  for (int k = iters - 1; k >= 0; --k) {
+    for (int i = 0; i < n; ++i)
+      GFD_ADJ_CK(cudaMemcpyAsync(uEcur[i], imgs[i].u_iters + (size_t)k * P, P * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, s));
+    const int rr = solve_batched_dev(c, n, rec.data(), 1, s);  // u_I, u_p, lambda of step k
+    if (rr != GFD_OK) return rr;
+    for (int i0 = 0; i0 < n;) {  // guided-filter adjoint, one launch per run of equal w
+      int i1 = i0 + 1;
+      while (i1 < n && imgs[i1].w == imgs[i0].w) ++i1;
+      GFD_ADJ_CK(launch_adj_guided_filter(d_desc + i0, i1 - i0, M, N, (imgs[i0].w - 1) / 2, s));
+      i0 = i1;
+    }
+    for (int op = 0; op < 5; ++op) GFD_ADJ_CK(fwd(op));
+    GFD_ADJ_CK(launch_adj_spectral(d_desc, n, M, N, c->d2, s));
+    GFD_ADJ_CK(adj(7));
+    GFD_ADJ_CK(launch_adj_next(d_desc, n, M, N, s));
+  }
+  GFD_ADJ_CK(adj(8));
+  GFD_ADJ_CK(adj(9));
+  GFD_ADJ_CK(launch_adj_final(d_desc, n, M, N, max_psf, s));
+#undef GFD_ADJ_CK
+  c->last_stream = s;
+  return GFD_OK;
+}
+
 int gfdeconv_solve(gfdeconv_ctx* c, const float* y, int M, int N, const float* h, int kh, int kw,
                    double sigma, int w, double eps, int iters, float* u_out, double* lambda_out,
                    double* isnr_out, const float* u_orig, const float* u_init, void* stream) {
@@ -1080,6 +1301,7 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return map_err(e);
     if (c->stage) cudaFree(c->stage);
+  if (c->adj_ws) cudaFree(c->adj_ws);
     c->stage = nullptr;
     c->stage_bytes = 0;
     if ((e = cudaMalloc(&c->stage, cur)) != cudaSuccess) return map_err(e);
@@ -1152,6 +1374,7 @@ int gfdeconv_solve_batched_host(gfdeconv_ctx* c, int n, const gfdeconv_image* im
       // ahead of every chain
       init_in.push_back(Cp{base + off_ui[i], (const char*)im.u_init, P});
     }
+    dev[i].u_iters = nullptr;  // checkpoints are a device-buffer feature
     dev[i].u_out = (float*)(base + off_u[i]);
     add(d2h_img[i], (char*)im.u_out, base + off_u[i], P);
     double* const outs[3] = {im.lambda_out, im.isnr_out, im.res_out};

@@ -153,6 +153,7 @@ struct ImgDesc {
   float2* YN;         // Y(k, N/2)
   double* part;       // per-item partial sums of a spectral pass, (KNODES+1) each
   double* rowsum;     // per-item sums of the iterate from the forward row pass
+  float* u_iters;     // [iters][M*N] the iterate entering each iteration, or null
 };
 
 // One size class of a batch: all images with the same canvas M x N.

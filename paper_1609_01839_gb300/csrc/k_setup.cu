@@ -225,6 +225,26 @@ cudaError_t launch_crop(const float* src, int N, float* dst, int m, int n, cudaS
   return cudaGetLastError();
 }
 
+// u_iters[k] <- u for every image of the class that keeps checkpoints.
+__global__ void k_save_iterate(ClassDesc cd, const ImgDesc* __restrict__ imgs, int k) {
+  const size_t P4 = (size_t)cd.M * cd.N / 4;
+  const size_t total = P4 * cd.n_img;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t li = idx / P4, i = idx - li * P4;
+    const ImgDesc& d = imgs[cd.img0 + li];
+    if (!d.u_iters) continue;
+    reinterpret_cast<float4*>(d.u_iters + (size_t)k * cd.M * cd.N)[i] =
+        __ldcg(reinterpret_cast<const float4*>(d.u) + i);
+  }
+}
+
+cudaError_t launch_save_iterate(const ClassLaunch& c, int k, cudaStream_t s) {
+  const size_t total = (size_t)c.cd.M * c.cd.N / 4 * c.cd.n_img;
+  k_save_iterate<<<plane_blocks(total), 256, 0, s>>>(c.cd, c.imgs, k);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
   const size_t P = (size_t)c.cd.M * c.cd.N;
   int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));
@@ -267,6 +287,7 @@ cudaError_t launch_unpack_dc(const ClassLaunch& c, cudaStream_t s) {
 cudaError_t configure_fft_kernels();
 cudaError_t configure_gf_kernel();
 cudaError_t configure_gfc_kernels();
+cudaError_t configure_adj_kernels();
 cudaError_t configure_df_kernels();
 
 cudaError_t configure_kernels() {
@@ -274,6 +295,7 @@ cudaError_t configure_kernels() {
   if (e != cudaSuccess) return e;
   if ((e = configure_df_kernels()) != cudaSuccess) return e;
   if ((e = configure_gfc_kernels()) != cudaSuccess) return e;
+  if ((e = configure_adj_kernels()) != cudaSuccess) return e;
   return configure_gf_kernel();
 }
 

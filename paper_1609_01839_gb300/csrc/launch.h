@@ -102,6 +102,43 @@ cudaError_t launch_pad_symmetric(const float* y, int m, int n, float* dst, int M
                                  cudaStream_t s);
 cudaError_t launch_crop(const float* src, int N, float* dst, int m, int n, cudaStream_t s);
 
+// Copy every image's iterate u_E into its checkpoint slot u_iters[k] (images
+// without u_iters are skipped).
+cudaError_t launch_save_iterate(const ClassLaunch& c, int k, cudaStream_t s);
+
+// Per-image state of a backward solve (k_adjoint.cu).  Real planes are M*N
+// floats, spectra packed row-major half spectra (M*N/2 float2).
+struct AdjDesc {
+  const float* y;
+  const float* h;
+  int kh, kw;
+  double sigma, eps, rho_fixed;
+  const float* uI;    // u_I, u_p of the recomputed forward step
+  const float* up;
+  float* gu;          // g_u of the step's output; then of its input
+  float *A, *MU, *PB, *VE;                    // a, mu, pbar, sigma^2 + eps
+  float *GI0, *GCOV, *GVAR, *GMU, *GPB;       // pointwise adjoints of Eq. 3-5
+  float *guI, *gup;                           // g_uI, g_up
+  float *gtmp, *gtmp2;                        // adjoint DFT results
+  float2 *H, *Y, *UE, *UI, *Up, *GUI, *GUp;   // spectra of the step
+  float2 *gUE, *gH, *gY;                      // their gradients
+  const double* lam;  // lambda of the step (+inf: u_E in K)
+  double* acc;        // g_lam, P f', c, g_T, sum y, sum y^2, sum |h|, g_num, g_den
+  double* g_eps;      // accumulated dL/deps
+  double* g_eps_out;  // caller outputs
+  float* gy_out;
+  float* gh_out;
+};
+constexpr int ADJ_ACC = 9;
+cudaError_t launch_adj_guided_filter(const AdjDesc* descs, int n, int M, int N, int rad,
+                                     cudaStream_t s);
+cudaError_t launch_adj_spectral(const AdjDesc* descs, int n, int M, int N, const float* d2tab,
+                                cudaStream_t s);
+cudaError_t launch_adj_next(const AdjDesc* descs, int n, int M, int N, cudaStream_t s);
+cudaError_t launch_adj_stats(const AdjDesc* descs, int n, int M, int N, cudaStream_t s);
+cudaError_t launch_adj_final(const AdjDesc* descs, int n, int M, int N, int max_psf,
+                             cudaStream_t s);
+
 // Opt every kernel into large dynamic shared memory (once per process/device).
 cudaError_t configure_kernels();
 

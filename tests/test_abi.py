@@ -95,4 +95,4 @@ def test_binding_struct_matches_header_layout(libpath):
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"[\w\*\s]+?\b(\w+)\s*[,;]", body)
     assert names == fields, (names, fields)
-    assert ctypes.sizeof(gfd.Image) == 8 + 4 + 4 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 8
+    assert ctypes.sizeof(gfd.Image) == 8 + 4 + 4 + 8 + 4 + 4 + 8 + 8 + 8 + 9 * 8

@@ -94,3 +94,24 @@ def test_gradient_64_crop_of_the_differentiation_workload():
         v = rng.standard_normal(y.shape)
         num = fd(lambda x: A.loss_only(x, h, s, w, eps, K, uc), y, v, 1e-6)
         assert np.sum(r["g_y"] * v) == pytest.approx(num, rel=RTOL)
+
+
+def test_gradient_through_the_infinite_lambda_branch():
+    """A trajectory whose first two steps take the lambda = inf branch (u_E
+    starts at the clean image, in the feasible set for sigma twice the noise)
+    and whose later steps solve Eq. 11: the branch steps pass the gradient
+    through the guided filter only."""
+    y, h, s, w, eps, K, uc = problem(64, 25, 1.6, 1.0 / 255.0, 7, 1e-3, 4, 11)
+    s2 = 2.0 * s
+    r = A.solve_with_grad(y, h, s2, w, eps, K, uc, u_init=uc)
+    assert np.isinf(r["lam"][0]) and np.isinf(r["lam"][1]) and np.isfinite(r["lam"][2])
+    num = fd(lambda e: A.loss_only(y, h, s2, w, e, K, uc, u_init=uc), eps, 1.0, 1e-7)
+    assert r["g_eps"] == pytest.approx(num, rel=RTOL)
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(y.shape)
+    num = fd(lambda x: A.loss_only(x, h, s2, w, eps, K, uc, u_init=uc), y, v, 1e-6)
+    assert np.sum(r["g_y"] * v) == pytest.approx(num, rel=RTOL)
+    e = np.zeros_like(h)
+    e[12, 12] = 1.0
+    num = fd(lambda x: A.loss_only(y, x, s2, w, eps, K, uc, u_init=uc), h, e, 1e-7)
+    assert r["g_h"][12, 12] == pytest.approx(num, rel=RTOL)
