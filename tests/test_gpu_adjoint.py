@@ -3,7 +3,7 @@ hand-written adjoint) against the oracle's FP64 gradient (oracle/adjoint.py,
 itself pinned by central finite differences) on the same FP32 inputs.
 
 Tolerance: the GPU's forward and backward run in FP32 spectra and planes
-with FP64 window sums and reductions; its gradients are held to 1e-3 relative
+with FP64 window sums and reductions; its gradients are held to 1e-4 relative
 in norm (g_y, g_h) and in value (g_eps) against the FP64 oracle (the bar the
 differentiation workload states for its finite-difference check; measured
 errors, recorded, are 4e-6 to 4e-5)."""
