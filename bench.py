@@ -113,6 +113,11 @@ def _gen_c4(j):
     return synthetic.config_c4_image(j, iters=C4_ITERS)
 
 
+def _gen_c3(i):
+    import synthetic
+    return synthetic.config_c3_image(i)
+
+
 def _gen_table1(t):
     import synthetic
     return synthetic.config_table1(t)
@@ -355,6 +360,51 @@ def run_large_leg(args, gfd, torch, dev, stream, var_mode, hbm_peak):
             "status_nonzero": sum(1 for s_ in st if s_ & ~gfd.STATUS_NONCONVERGED)}
 
 
+def run_diff_leg(args, gfd, torch, dev, stream):
+    """The differentiation workload: 16 images of 512^2 (25 x 25 Gaussian PSF,
+    noise 1/255, w = 7, eps = 1e-3), 10 iterations; one step = the forward
+    solve keeping per-iteration checkpoints plus the backward pass to dL/dy,
+    dL/dh, dL/deps of L = MSE(u^10, u_clean) (dL/du formed with torch)."""
+    with mp.get_context("spawn").Pool(8) as pool:
+        probs = pool.map(_gen_c3, range(16))
+    iters = probs[0].iters
+    items = [{"y": torch.from_numpy(p.y).to(dev), "h": torch.from_numpy(p.h).to(dev),
+              "sigma": p.sigma, "w": p.w, "eps": p.eps} for p in probs]
+    clean = [torch.from_numpy(p.u_orig).to(dev) for p in probs]
+    ctx = gfd.Context(dev.index or 0)
+    P = probs[0].y.size
+
+    def step():
+        ctx.solve_batched(items, iters, stream=stream, want_checkpoints=True)
+        g_us = [2.0 * (it["u"] - c) / P for it, c in zip(items, clean)]
+        return ctx.backward_batched(items, iters, g_us, stream)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    fwd_ms = bwd_ms = 0.0
+    for _ in range(steps):
+        e0.record(stream)
+        ctx.solve_batched(items, iters, stream=stream, want_checkpoints=True)
+        e1.record(stream)
+        g_us = [2.0 * (it["u"] - c) / P for it, c in zip(items, clean)]
+        ctx.backward_batched(items, iters, g_us, stream)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms += e0.elapsed_time(e1) / steps
+        bwd_ms += e1.elapsed_time(e2) / steps
+    ctx.close()
+    px = sum(p.y.size for p in probs) * iters
+    return {"workload": "differentiation_16x512^2_gauss25_10it", "unit": UNIT,
+            "value_forward_backward": px / ((fwd_ms + bwd_ms) / 1e3) / 1e6,
+            "ms_forward_with_checkpoints": fwd_ms, "ms_backward": bwd_ms,
+            "note": "value = pixel-iterations of the forward per second of forward + backward"}
+
+
 def run_table1(args):
     """The paper's five Table 1 settings on synthetic 256^2 stand-ins, solved
     as one batch on the GPU; per setting the lambda and ISNR curves and the
@@ -535,6 +585,9 @@ def run_ours(args):
     large = None
     if rank == 0 and not args.no_large:
         large = run_large_leg(args, gfd, torch, dev, stream, ctx_var, hbm_peak)
+    diff = None
+    if rank == 0 and not args.no_diff:
+        diff = run_diff_leg(args, gfd, torch, dev, stream)
 
     # parity spot check + CPU baseline: one image of each size class, oracle FP64
     cpu = None
@@ -581,6 +634,7 @@ def run_ours(args):
         "plain": {"value": plain_value, "unit": UNIT, "images": plain_n,
                   "batched_over_plain": value / world / plain_value},
         "cpu_baseline": cpu, "parity_vs_oracle": parity, "large_image": large,
+        "differentiation": diff,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps, "runs": e2e_reps,
                 "of_runs": "median"},
@@ -618,6 +672,8 @@ def main(argv=None):
                          "instead of tuning")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4 x 4096^2 bandwidth-stress leg")
+    ap.add_argument("--no-diff", action="store_true",
+                    help="skip the differentiation leg (forward + backward)")
     ap.add_argument("--table1", action="store_true",
                     help="run the Table 1 settings sweep instead of the benchmark")
     ap.add_argument("--workload", choices=["batch", "large"], default="batch",

@@ -90,9 +90,11 @@ typedef struct {
    * same batch (pointers, sizes, parameters) is solved again. */
   int use_graphs;
   /* Spectral passes of Eq. 11 launched per iteration after the one fused
-   * into the forward transform (images whose root is resolved skip them);
-   * <= 0 selects 4, at most 16.  If an image's root is still bracketed after
-   * the last one, GFD_STATUS_PASSES_EXHAUSTED is set. */
+   * into the forward transform (images whose root is resolved skip them) in
+   * iterations 0-2, whose brackets are wide; later iterations, whose bracket
+   * is centred on the extrapolated root, launch at most 2.  <= 0 selects 4,
+   * at most 16.  If an image's root is still bracketed after the last pass of
+   * an iteration, GFD_STATUS_PASSES_EXHAUSTED is set. */
   int lambda_max_passes;
   /* Relative width of the final lambda bracket (the root search stops below
    * it); <= 0 selects 1e-13, else in [1e-14, 1e-2]. */

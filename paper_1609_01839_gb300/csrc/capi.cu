@@ -22,6 +22,8 @@ using namespace gfd;
 namespace {
 
 constexpr int AUX_SLOTS = 8;
+// Fallback lambda passes launched per iteration from the fourth iteration on.
+constexpr int LATE_LAMBDA_PASSES = 2;
 constexpr int CHAINS = GFD_CHAINS;
 
 // A host <-> device copy that the host entry point asks a solve to issue.
@@ -459,10 +461,13 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
         GFD_T(GFD_PHASE_COL_FWD_LAMBDA, launch_col_fwd_lambda(cl, t, k, s));
         L += 2;
       }
-      for (int p = 1; p <= passes; ++p)
+      // iterations 0-2 start from wide brackets; later ones from the
+      // extrapolated root, which the fused pass almost always resolves
+      const int npass = k < 3 ? passes : std::min(passes, LATE_LAMBDA_PASSES);
+      for (int p = 1; p <= npass; ++p)
         for (auto& cl : classes) {
           if (tm) tm->cur_cls = cl.class_id;
-          GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == passes, s));
+          GFD_T(GFD_PHASE_LAMBDA_PASS, launch_lambda_pass(cl, k, p == npass, s));
           ++L;
         }
       for (auto& cl : classes) {

@@ -26,7 +26,7 @@ __all__ = [
     "psf_uniform", "psf_inv_quadratic", "psf_gaussian", "psf_binomial5",
     "psf_motion", "blur_circular", "sigma_from_bsnr", "mirror_extend",
     "config_c0", "config_c1", "config_c2_image", "config_c2", "config_c4",
-    "config_c4_image", "config_table1", "table1_psf", "next_pow2",
+    "config_c4_image", "config_table1", "config_c3_image", "table1_psf", "next_pow2",
 ]
 
 
@@ -371,6 +371,20 @@ def config_c4_image(j: int, size: int = 4096, iters: int = 30) -> Problem:
     y, sigma = _degrade(u, h, rng, bsnr_db=35.0)
     return Problem(_f32(y), _f32(h), sigma, 9, 1e-4, iters, _f32(u), (size, size),
                    {"name": f"c4_{j}"})
+
+
+def config_c3_image(i: int, size: int = 512, iters: int = 10) -> Problem:
+    """Differentiation workload, image i (seed 3000 + i): piecewise-smooth
+    content as in the 512^2 workload, 25 x 25 Gaussian PSF with sigma 1.6,
+    AWGN sigma = 1/255, w = 7, eps = 1e-3, 10 iterations; the loss is the MSE
+    of u^10 against the clean image."""
+    seed = 3000 + i
+    rng = np.random.default_rng(seed)
+    u = image_polygons(seed, size, size, n_poly=30, texture_std=0.02, rng=rng)
+    h = psf_gaussian(25, 1.6)
+    y, sigma = _degrade(u, h, rng, sigma=1.0 / 255.0)
+    return Problem(_f32(y), _f32(h), sigma, 7, 1e-3, iters, _f32(u), (size, size),
+                   {"name": f"c3_{i}"})
 
 
 def config_table1(test: int, seed: int = 0, M: int = 256, N: int = 256,
