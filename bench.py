@@ -405,6 +405,18 @@ def run_diff_leg(args, gfd, torch, dev, stream):
             "note": "value = pixel-iterations of the forward per second of forward + backward"}
 
 
+def run_diff_only(args):
+    """Profiler mode: the differentiation leg alone, as one JSON line."""
+    import torch
+    import paper_1609_01839_gb300 as gfd
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"differentiation": run_diff_leg(args, gfd, torch, dev,
+                                                      torch.cuda.current_stream(dev))}),
+          flush=True)
+    return 0
+
+
 def run_table1(args):
     """The paper's five Table 1 settings on synthetic 256^2 stand-ins, solved
     as one batch on the GPU; per setting the lambda and ISNR curves and the
@@ -676,8 +688,9 @@ def main(argv=None):
                     help="skip the differentiation leg (forward + backward)")
     ap.add_argument("--table1", action="store_true",
                     help="run the Table 1 settings sweep instead of the benchmark")
-    ap.add_argument("--workload", choices=["batch", "large"], default="batch",
-                    help="with --only-solve: the 256-image batch or the 4 x 4096^2 batch")
+    ap.add_argument("--workload", choices=["batch", "large", "diff"], default="batch",
+                    help="with --only-solve: the 256-image batch, the 4 x 4096^2 batch, or "
+                         "the differentiation workload (forward + backward)")
     ap.add_argument("--iters", type=int, default=0,
                     help="with --only-solve: iterations per solve (0 = the workload's)")
     args = ap.parse_args(argv)
@@ -687,6 +700,8 @@ def main(argv=None):
         return run_table1(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_solve and args.workload == "diff":
+        return run_diff_only(args)
     return run_ours(args)
 
 

@@ -295,17 +295,18 @@ int gfdeconv_tune_get(gfdeconv_ctx* ctx, int M, int N, int* col_threads, int* ro
 /* Reverse mode of the unrolled method: given dL/du^K for each image, the
  * gradients dL/dy, dL/dh and dL/deps of a loss L of the result u^K of
  * `iters` iterations (Sec. 3.1 Steps 0-3 with Sec. 3.2's lambda).  `imgs`
- * are the descriptors of a gfdeconv_solve_batched call with u_iters set (its
- * checkpoints are read, nothing else of its outputs); all images share one
- * canvas size, windows are periodic (gfdeconv_opts.boundary = 0).  Each
- * iteration is recomputed from its checkpoint and undone in reverse: the
- * guided filter (Eq. 3-5), the spectral solves (Eq. 8-9), lambda through the
- * implicit derivative of Eq. 11 (where lambda = inf, u_E in K, lambda is a
- * constant and u_I = u_p = u_E), the DFTs; H, Y and T = rho P sigma^2
- * (Eq. 12) collect their gradients over the iterations.  FP32 spectra and
- * planes, FP64 window sums and reductions.  The context's cached solve plan is
- * replaced.  Returns GFD_ERR_INVALID_ARG for missing checkpoints or mixed
- * canvas sizes. */
+ * are the descriptors of a completed gfdeconv_solve_batched call with u_iters
+ * and lambda_out set (the checkpoints u_E^k and the lambda_k it wrote are
+ * read, nothing else of its outputs); all images share one canvas size,
+ * windows are periodic (gfdeconv_opts.boundary = 0).  Each iteration is
+ * recomputed from its checkpoint with its lambda_k (U_E, Eq. 8-9, u_I and
+ * u_p) and undone in reverse: the guided filter (Eq. 3-5), the spectral
+ * solves (Eq. 8-9), lambda through the implicit derivative of Eq. 11 (where
+ * lambda = inf, u_E in K, lambda is a constant and u_I = u_p = u_E), the
+ * DFTs; H, Y and T = rho P sigma^2 (Eq. 12) collect their gradients over the
+ * iterations.  FP32 spectra and planes, compensated (double-float) window
+ * sums, FP64 sums over bins and pixels.  Returns GFD_ERR_INVALID_ARG for
+ * missing checkpoints or lambdas, or mixed canvas sizes. */
 int gfdeconv_backward_batched(gfdeconv_ctx* ctx, int n, const gfdeconv_image* imgs,
                               const gfdeconv_grad* grads, int iters, void* stream);
 

@@ -42,6 +42,7 @@ VAR_NAMES = {VAR_COMPENSATED: "compensated_split", VAR_FP64: "fp64", VAR_FP32: "
 # guided-filter window boundary (gfdeconv_opts.boundary)
 BOUNDARY_PERIODIC = 0
 BOUNDARY_TRUNCATED = 1
+ERR_INVALID_ARG = -1    # argument errors, returned before any launch
 ERR_SCRATCH_LIMIT = -8  # gfdeconv_fft2_r2c_noalloc: M*N above its static scratch
 NUM_PHASES = 8
 PHASES = ("setup", "row_fwd", "col_fwd_lambda", "lambda_pass", "col_solve_inv", "row_inv",
@@ -327,6 +328,7 @@ class Context:
             a.sigma, a.w, a.eps = float(it["sigma"]), int(it["w"]), float(it["eps"])
             a.u_out = _ptr(it["u"], "u", torch.float32, M * N)
             a.u_iters = _ptr(it["u_iters"], "u_iters", torch.float32)
+            a.lambda_out = _ptr(it["lam"], "lambda")
             gy = torch.empty_like(y)
             gh = torch.empty_like(h)
             ge = torch.empty((), dtype=torch.float64, device=y.device)

@@ -1037,7 +1037,8 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
     int r = validate_image(imgs[i], iters);
     if (r == GFD_OK) r = validate_device_planes(imgs[i]);
     if (r != GFD_OK) return r;
-    if (imgs[i].M != M || imgs[i].N != N || !imgs[i].u_iters) return GFD_ERR_INVALID_ARG;
+    if (imgs[i].M != M || imgs[i].N != N || !imgs[i].u_iters || !imgs[i].lambda_out)
+      return GFD_ERR_INVALID_ARG;
     const gfdeconv_grad& g = grads[i];
     if (!g.g_u || !g.g_y || !g.g_h || !g.g_eps || !aligned16(g.g_u) || !aligned16(g.g_y))
       return GFD_ERR_INVALID_ARG;
@@ -1046,10 +1047,10 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   if (cudaSetDevice(c->device) != cudaSuccess) return GFD_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)M * N;
-  // per image: 18 real planes (16 of the adjoint, u_E^k, the recomputed u) and
-  // 11 spectra (10 of the adjoint, the FFT scratch) of P floats each, 12
-  // doubles (lambda, g_eps, the sums)
-  const int n_real = 18, n_spec = 11, n_dbl = 12;
+  // per image: 17 real planes (16 of the adjoint, u_E^k) and 11 spectra (10
+  // of the adjoint, the FFT scratch) of P floats each, 12 doubles (lambda,
+  // g_eps, the sums)
+  const int n_real = 17, n_spec = 11, n_dbl = 12;
   const size_t plane = align256(P * sizeof(float));
   const size_t per_img = (n_real + n_spec) * plane + align256(n_dbl * sizeof(double));
   const size_t descs_bytes = align256(sizeof(AdjDesc) * n);
@@ -1072,9 +1073,8 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   const size_t fft_stride = align256(sizeof(ImgDesc) * n) / sizeof(ImgDesc);
   cur += fft_bytes;
   std::vector<AdjDesc> ad(n);
-  std::vector<float*> uEcur(n), ucur(n), hc(n), scratch(n);
+  std::vector<float*> uEcur(n), hc(n), scratch(n);
   std::vector<std::vector<ImgDesc>> fd(n_fft, std::vector<ImgDesc>(n));
-  std::vector<gfdeconv_image> rec(imgs, imgs + n);  // the recomputed forward steps
   for (int i = 0; i < n; ++i) {
     char* b = cur + per_img * i;
     auto realp = [&](int k) { return reinterpret_cast<float*>(b + plane * k); };
@@ -1108,7 +1108,6 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
     a.gtmp = realp(14);
     a.gtmp2 = realp(15);
     uEcur[i] = realp(16);
-    ucur[i] = realp(17);
     a.H = specp(0);
     a.Y = specp(1);
     a.UE = specp(2);
@@ -1121,23 +1120,13 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
     a.gY = specp(9);
     scratch[i] = reinterpret_cast<float*>(specp(10));
     hc[i] = a.gtmp2;  // the embedded PSF, transformed before gtmp2 is needed
+    a.lam_hist = imgs[i].lambda_out;
     a.lam = dbl;
     a.g_eps = dbl + 1;
     a.acc = dbl + 2;  // ADJ_ACC (9) doubles
     a.g_eps_out = grads[i].g_eps;
     a.gy_out = grads[i].g_y;
     a.gh_out = grads[i].g_h;
-    // the forward step recomputed from u_E^k (copied into uEcur each step)
-    gfdeconv_image& r = rec[i];
-    r.u_init = uEcur[i];
-    r.u_out = ucur[i];
-    r.uI_out = uIp;
-    r.up_out = upp;
-    r.lambda_out = dbl;
-    r.isnr_out = nullptr;
-    r.res_out = nullptr;
-    r.u_orig = nullptr;
-    r.u_iters = nullptr;
     // DFT descriptors: r2c(src -> dst) uses u, S, Y; c2r(src -> dst) uses QI, uI
     auto r2c = [&](int op, const float* src, float2* dst) {
       ImgDesc& q = fd[op][i];
@@ -1153,8 +1142,8 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
       q.uI = dst;
     };
     r2c(0, uEcur[i], a.UE);
-    r2c(1, uIp, a.UI);
-    r2c(2, upp, a.Up);
+    c2r(1, a.UI, uIp);  // the recomputed step: U_I, U_p -> u_I, u_p
+    c2r(2, a.Up, upp);
     r2c(3, a.guI, a.GUI);
     r2c(4, a.gup, a.GUp);
     r2c(5, hc[i], a.H);
@@ -1190,12 +1179,15 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
     if (r == cudaSuccess) r = launch_col_plain(cl, t, SEL_S, SEL_YS, false, s);
     return r;
   };
-  auto adj = [&](int op) -> cudaError_t {  // F^H of a packed Hermitian spectrum (scale 1)
+  // scale * F^H of a packed Hermitian spectrum (in place on the spectrum):
+  // scale 1 is the adjoint DFT, 1/P the inverse
+  auto adj = [&](int op, float scale) -> cudaError_t {
     const ClassLaunch cl = cls(op);
     cudaError_t r = launch_col_plain(cl, t, SEL_QI, SEL_QI, true, s);
-    if (r == cudaSuccess) r = launch_row_c2r(cl, t, SEL_QI, -1, SEL_UI, -1, 1.0f, s);
+    if (r == cudaSuccess) r = launch_row_c2r(cl, t, SEL_QI, -1, SEL_UI, -1, scale, s);
     return r;
   };
+  const float invP = 1.0f / (float)P;
 #define GFD_ADJ_CK(x)                    \
   do {                                   \
     if ((e = (x)) != cudaSuccess) return map_err(e); \
@@ -1214,24 +1206,29 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   GFD_ADJ_CK(launch_adj_stats(d_desc, n, M, N, s));
   // the steps, last first
   for (int k = iters - 1; k >= 0; --k) {
+    // recompute the step from u_E^k and the forward's lambda_k: U_E, then
+    // U_I, U_p (Eq. 8-9) and u_I, u_p
     for (int i = 0; i < n; ++i)
       GFD_ADJ_CK(cudaMemcpyAsync(uEcur[i], imgs[i].u_iters + (size_t)k * P, P * sizeof(float),
                                  cudaMemcpyDeviceToDevice, s));
-    const int rr = solve_batched_dev(c, n, rec.data(), 1, s);  // u_I, u_p, lambda of step k
-    if (rr != GFD_OK) return rr;
+    GFD_ADJ_CK(fwd(0));
+    GFD_ADJ_CK(launch_adj_recompute(d_desc, n, M, N, k, c->d2, s));
+    GFD_ADJ_CK(adj(1, invP));
+    GFD_ADJ_CK(adj(2, invP));
     for (int i0 = 0; i0 < n;) {  // guided-filter adjoint, one launch per run of equal w
       int i1 = i0 + 1;
       while (i1 < n && imgs[i1].w == imgs[i0].w) ++i1;
       GFD_ADJ_CK(launch_adj_guided_filter(d_desc + i0, i1 - i0, M, N, (imgs[i0].w - 1) / 2, s));
       i0 = i1;
     }
-    for (int op = 0; op < 5; ++op) GFD_ADJ_CK(fwd(op));
+    GFD_ADJ_CK(fwd(3));
+    GFD_ADJ_CK(fwd(4));
     GFD_ADJ_CK(launch_adj_spectral(d_desc, n, M, N, c->d2, s));
-    GFD_ADJ_CK(adj(7));
+    GFD_ADJ_CK(adj(7, 1.0f));
     GFD_ADJ_CK(launch_adj_next(d_desc, n, M, N, s));
   }
-  GFD_ADJ_CK(adj(8));
-  GFD_ADJ_CK(adj(9));
+  GFD_ADJ_CK(adj(8, 1.0f));
+  GFD_ADJ_CK(adj(9, 1.0f));
   GFD_ADJ_CK(launch_adj_final(d_desc, n, M, N, max_psf, s));
 #undef GFD_ADJ_CK
   c->last_stream = s;

@@ -13,6 +13,7 @@
 // contiguous run of rpc * TB values per tile.  TB = N/2 is plain row-major.
 #include "fft.cuh"
 #include "lambda.cuh"
+#include "spectral.cuh"
 #include "launch.h"
 
 namespace gfd {
@@ -300,14 +301,6 @@ __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
   }
 }
 
-// unpack bins (k, 0) and (k, N/2) from packed column values S[k], S[-k]
-GFD_D void unpack_pair(float2 Sk, float2 Smk, float2& A, float2& Bv) {
-  const float2 c = cconj(Smk);
-  A = cscale(cadd(Sk, c), 0.5f);
-  const float2 D = csub(Sk, c);
-  Bv = make_float2(0.5f * D.y, -0.5f * D.x);  // D / (2i)
-}
-
 // Forward column FFT of the iterate's row spectra (in place on S), fused with
 // the first evaluation of Eq. 11 at the nodes of the image's bracket.  Only
 // the S tile lands in shared memory; it is consumed by the first FFT stage,
@@ -563,29 +556,6 @@ k_lambda_pass(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st, int 
   }
 }
 
-// Eq. 9 (u_p) and Eq. 8 (u_I) at one bin:
-//   U_p = (conj(H) Y + lam U_E) / (|H|^2 + lam)
-//   U_I = (conj(H) Y + lam D2 U_E) / (|H|^2 + lam D2),  D2 = |F(nabla)|^2.
-GFD_D void solve_bin(float2 U, float2 H, float2 Y, float lam, float D2, bool branch,
-                     float2& UI, float2& Up) {
-  if (branch) {  // lambda = inf: u_I = u_p = u_E (Sec. 3.2)
-    UI = U;
-    Up = U;
-    return;
-  }
-  const float2 HY = make_float2(fmaf(H.x, Y.x, H.y * Y.y), fmaf(H.x, Y.y, -H.y * Y.x));
-  const float a = fmaf(H.x, H.x, H.y * H.y);
-  const float ip = __frcp_rn(a + lam);
-  Up = make_float2(fmaf(lam, U.x, HY.x) * ip, fmaf(lam, U.y, HY.y) * ip);
-  const float lg = lam * D2;
-  const float den = a + lg;
-  if (den > 0.0f) {
-    const float ii = __frcp_rn(den);
-    UI = make_float2(fmaf(lg, U.x, HY.x) * ii, fmaf(lg, U.y, HY.y) * ii);
-  } else {
-    UI = U;
-  }
-}
 
 // Spectral solves fused with the inverse column FFTs: an item's U_E tile
 // lands in shared memory (H and Y are read from global memory next to it);

@@ -122,7 +122,8 @@ struct AdjDesc {
   float *gtmp, *gtmp2;                        // adjoint DFT results
   float2 *H, *Y, *UE, *UI, *Up, *GUI, *GUp;   // spectra of the step
   float2 *gUE, *gH, *gY;                      // their gradients
-  const double* lam;  // lambda of the step (+inf: u_E in K)
+  const double* lam_hist;  // lambda_k of the forward solve, k = 0..iters-1
+  double* lam;        // lambda of the step (+inf: u_E in K)
   double* acc;        // g_lam, P f', c, g_T, sum y, sum y^2, sum |h|, g_num, g_den
   double* g_eps;      // accumulated dL/deps
   double* g_eps_out;  // caller outputs
@@ -132,6 +133,10 @@ struct AdjDesc {
 constexpr int ADJ_ACC = 9;
 cudaError_t launch_adj_guided_filter(const AdjDesc* descs, int n, int M, int N, int rad,
                                      cudaStream_t s);
+// Start of backward step k: lambda_k into every image's state, and the
+// spectra U_I, U_p (Eq. 8-9) of the step from U_E, H, Y into UI, Up.
+cudaError_t launch_adj_recompute(const AdjDesc* descs, int n, int M, int N, int k,
+                                 const float* d2tab, cudaStream_t s);
 cudaError_t launch_adj_spectral(const AdjDesc* descs, int n, int M, int N, const float* d2tab,
                                 cudaStream_t s);
 cudaError_t launch_adj_next(const AdjDesc* descs, int n, int M, int N, cudaStream_t s);
