@@ -13,28 +13,57 @@ GFD_D df warp_sum_df(df v) {
   return v;
 }
 
-// Sum y, y^2, (y - u_orig)^2 over each image, and sum h, sum |h|.  The
-// per-thread and per-block sums are double-float (each square formed exactly
-// by a two-product, each difference by a two-sum), so no FP64 instruction
-// runs per pixel; the per-block results are added in FP64.  grid (chunks, n_img).
+// Sum y, y^2, (y - u_orig)^2 over each image, and sum h, sum |h|.  Each
+// thread keeps compensated sums (an FP32 running sum plus the exact rounding
+// errors of its additions, summed apart; each square formed exactly by a
+// two-product, each difference by a two-sum) over float4 groups, so no FP64
+// instruction runs per pixel; warps and blocks add double-float values, and
+// the per-block results are added in FP64.  grid (chunks, n_img).
+struct CAcc {
+  float hi = 0.0f, lo = 0.0f;
+  GFD_D void add(float v) {
+    const df t = two_sum(hi, v);
+    hi = t.hi;
+    lo += t.lo;
+  }
+  GFD_D void add(df v) {
+    const df t = two_sum(hi, v.hi);
+    hi = t.hi;
+    lo += t.lo + v.lo;
+  }
+  GFD_D df get() const { return two_sum(hi, lo); }
+};
+
 __global__ void k_setup_stats(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st) {
   __shared__ df red[3][32];
   const int gi = cd.img0 + blockIdx.y;
   const ImgDesc& d = imgs[gi];
-  const size_t P = (size_t)cd.M * cd.N;
-  df sy{0.0f, 0.0f}, syy{0.0f, 0.0f}, se{0.0f, 0.0f};
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+  const size_t P4 = (size_t)cd.M * cd.N / 4;
+  const float4* y4 = reinterpret_cast<const float4*>(d.y);
+  const float4* o4 = reinterpret_cast<const float4*>(d.uo);
+  CAcc ay, ayy, ae;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P4;
        i += (size_t)gridDim.x * blockDim.x) {
-    const float v = __ldg(&d.y[i]);
-    sy = df_add(sy, df_make(v));
-    syy = df_add(syy, two_prod(v, v));
-    if (d.uo) {
-      const df e = two_sum(v, -__ldg(&d.uo[i]));  // exact difference
-      df e2 = two_prod(e.hi, e.hi);
-      e2.lo = fmaf(2.0f * e.hi, e.lo, e2.lo);
-      se = df_add(se, quick_two_sum(e2.hi, e2.lo));
+    const float4 v4 = __ldg(&y4[i]);
+    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (o4) {
+      const float4 q = __ldg(&o4[i]);
+      o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ay.add(v[k]);
+      ayy.add(two_prod(v[k], v[k]));
+      if (o4) {
+        const df e = two_sum(v[k], -o[k]);  // exact difference
+        df e2 = two_prod(e.hi, e.hi);
+        e2.lo = fmaf(2.0f * e.hi, e.lo, e2.lo);
+        ae.add(e2);
+      }
     }
   }
+  df sy = ay.get(), syy = ayy.get(), se = ae.get();
   sy = warp_sum_df(sy);
   syy = warp_sum_df(syy);
   se = warp_sum_df(se);
@@ -247,8 +276,8 @@ cudaError_t launch_save_iterate(const ClassLaunch& c, int k, cudaStream_t s) {
 
 cudaError_t launch_setup_stats(const ClassLaunch& c, cudaStream_t s) {
   const size_t P = (size_t)c.cd.M * c.cd.N;
-  int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));
-  if (chunks > 64) chunks = 64;
+  int chunks = (int)((P + 256 * 16 - 1) / (256 * 16));  // 4 float4 groups per thread
+  if (chunks > 1024) chunks = 1024;
   k_setup_stats<<<dim3(chunks, c.cd.n_img), 256, 0, s>>>(c.cd, c.imgs, c.st);
   return cudaGetLastError();
 }

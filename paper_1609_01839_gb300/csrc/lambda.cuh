@@ -211,23 +211,39 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
 // Root of the interpolant in t = ln(lambda) through (t_m, g_m), m < KNODES,
 // t_m = ln(x_m) of the FP32 node values x_m (ascending; g increasing through
 // 0 between x_j and x_{j+1}).  Lane m < KNODES holds (x_m, g_m).  The
-// logarithms are formed in FP64 and carried as double-float; barycentric
-// weights and the interpolant are formed in double-float; the root is
-// bracketed by multisection: every lane evaluates the sign of the
-// interpolant at its own trial point, and the bracket shrinks 33-fold per
-// round.  Returns lambda = exp(t_root).
+// logarithms are formed in FP64 and carried as double-float, as are the
+// barycentric weights w_m = 1 / prod_{n != m} (t_m - t_n) of the actual nodes.
+// Inside (t_j, t_{j+1}) the interpolant is p(t) = l(t) S(t) with
+// l(t) = prod_m (t - t_m), whose sign there is (-1)^(KNODES-1-j), and
+// S(t) = sum_m w_m g_m / (t - t_m) (the first barycentric form), so the sign
+// of p at a point needs S alone, one double-float quotient per node.  The
+// root is bracketed by multisection: every lane evaluates the sign at its own
+// trial point and the bracket shrinks to the two trial points that straddle
+// the root.  After a plain round (32 points across the bracket) the next
+// round's points sit in a window about the secant estimate from p at the
+// bracket's ends (window half-width 1/16, then 1/256, then 1/4096 of the
+// bracket while the root keeps falling inside it; a round whose window misses
+// still leaves a valid bracket, and the next round is plain again).  Returns
+// lambda = exp(t_root) at the bracket's midpoint once its width is <= rtol.
+GFD_D df df_div_fast(df a, df b) {  // a / b, error ~2^-44 relative
+  const float ib = __fdividef(1.0f, b.hi);
+  const float q1 = a.hi * ib;
+  const df p = two_prod(b.hi, q1);
+  const float r = ((a.hi - p.hi) - p.lo + a.lo) - q1 * b.lo;  // a - q1 b
+  return quick_two_sum(q1, r * ib);
+}
+
 GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) {
   const bool own = lane < KNODES;
   const df tm = own ? df_from_double(log((double)xm)) : df_make(0.0f);
-  // All abscissa differences are scaled by a power of two ~ 1/(bracket
-  // width): exact, and it keeps the products of 11 differences in FP32
-  // range (the barycentric ratio does not depend on the scale).
+  // All abscissa differences are scaled by a power of two ~ 1/(node span):
+  // exact, and it keeps the products of 11 differences in FP32 range (the
+  // sign of S and the root do not depend on the scale).
   const float t0 = __shfl_sync(0xffffffffu, tm.hi, 0);
   const float tK = __shfl_sync(0xffffffffu, tm.hi, KNODES - 1);
   int ex;
   frexpf(tK - t0, &ex);
   const float sc = ldexpf(1.0f, -ex);
-  // weight w_m = 1 / prod_{n != m} (t_m - t_n), differences in double-float
   df prod = df_make(1.0f);
   for (int n = 0; n < KNODES; ++n) {
     const df tn{__shfl_sync(0xffffffffu, tm.hi, n), __shfl_sync(0xffffffffu, tm.lo, n)};
@@ -236,44 +252,84 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) 
       prod = df_mul(prod, df{dd.hi * sc, dd.lo * sc});
     }
   }
-  const df w = own ? df_rcp(prod) : df_make(0.0f);
-  __shared__ df s_t[KNODES], s_w[KNODES];
+  const df c = own ? df_mul_f(df_rcp(prod), gm) : df_make(0.0f);  // w_m g_m
+  __shared__ df s_t[KNODES], s_c[KNODES];
   __shared__ float s_g[KNODES];
   if (own) {
     s_t[lane] = tm;
+    s_c[lane] = c;
     s_g[lane] = gm;
-    s_w[lane] = w;
   }
   __syncwarp();
+  const float sig = ((KNODES - 1 - j) & 1) ? -1.0f : 1.0f;  // sign of l(t) in the bracket
   df a = s_t[j], b = s_t[j + 1];
-  for (int round = 0; round < 10; ++round) {
-    // trial point a + (b - a) (lane + 1) / 33
+  float pa = s_g[j], pb = s_g[j + 1];  // p at the bracket's ends
+  int level = 0;                       // windows in a row that held the root
+  const float frac32 = (float)(lane + 1) / 33.0f;
+  for (int round = 0; round < 24; ++round) {
     const df width = df_sub(b, a);
-    const df t = df_add(a, df_mul_f(width, (float)(lane + 1) / 33.0f));
-    df num = df_make(0.0f), den = df_make(0.0f);
+    if (df_to_double(width) <= rtol) break;  // absolute in t: relative in lambda
+    // trial points: across the bracket, or across a window about the secant
+    // estimate of the root
+    df wlo = a, ww = width;
+    if (level > 0) {
+      const float est = pa / (pa - pb);
+      if (est > 0.0f && est < 1.0f) {
+        const float h = level == 1 ? 0.0625f : (level == 2 ? 0.00390625f : 0.000244140625f);
+        const float f0 = fmaxf(est - h, 0.0f), f1 = fminf(est + h, 1.0f);
+        wlo = df_add(a, df_mul_f(width, f0));
+        ww = df_mul_f(width, f1 - f0);
+      } else {
+        level = 0;
+      }
+    }
+    const df t = df_add(wlo, df_mul_f(ww, frac32));
+    df S0 = df_make(0.0f), S1 = df_make(0.0f);  // two partial sums (shorter chains)
+    float ell = 1.0f;
     bool at_node = false;
     float node_g = 0.0f;
-    for (int m = 0; m < KNODES; ++m) {
-      const df dd = df_sub(t, s_t[m]);
-      if (dd.hi == 0.0f) {
+    // add node m's term w_m g_m / (t - t_m) to S (t at a node: p(t) = g_m)
+    auto term = [&](int m, df& S) {
+      const df tmm = s_t[m];
+      df d = two_sum(t.hi, -tmm.hi);
+      d.lo += t.lo - tmm.lo;
+      if (d.hi == 0.0f && d.lo == 0.0f) {
         at_node = true;
         node_g = s_g[m];
-        continue;
+        return;
       }
-      const df d{dd.hi * sc, dd.lo * sc};
-      const df q = df_mul(s_w[m], df_rcp(d));
-      num = df_add(num, df_mul_f(q, s_g[m]));
-      den = df_add(den, q);
+      d = quick_two_sum(d.hi, d.lo);
+      d.hi *= sc;
+      d.lo *= sc;
+      ell *= d.hi;
+      const df q = df_div_fast(s_c[m], d);
+      const df u = two_sum(S.hi, q.hi);
+      S.hi = u.hi;
+      S.lo += u.lo + q.lo;
+    };
+#pragma unroll 2
+    for (int m = 0; m < KNODES; m += 2) {  // registers stay low in the pass kernels
+      term(m, S0);
+      term(m + 1, S1);
     }
-    const bool neg = at_node ? (node_g < 0.0f) : ((num.hi < 0.0f) != (den.hi < 0.0f));
+    const df Sv = df_add(quick_two_sum(S0.hi, S0.lo), quick_two_sum(S1.hi, S1.lo));
+    const bool neg = at_node ? (node_g < 0.0f) : (sig * Sv.hi < 0.0f);
+    const float pv = at_node ? node_g : ell * (Sv.hi + Sv.lo);  // p(t), for the estimate
     const unsigned below = __ballot_sync(0xffffffffu, neg);
     // the interpolant increases: trial points below the root form a prefix
     const int nb = __popc(below);  // lanes 0..nb-1 are below the root
-    const df na = nb > 0 ? df_add(a, df_mul_f(width, (float)nb / 33.0f)) : a;
-    const df nbv = nb < 32 ? df_add(a, df_mul_f(width, (float)(nb + 1) / 33.0f)) : b;
-    a = na;
-    b = nbv;
-    if (df_to_double(df_sub(b, a)) <= rtol) break;  // absolute in t: relative in lambda
+    const float p_lo = __shfl_sync(0xffffffffu, pv, nb > 0 ? nb - 1 : 0);
+    const float p_hi = __shfl_sync(0xffffffffu, pv, nb < 32 ? nb : 31);
+    const bool hit = nb > 0 && nb < 32;  // the root lies between two trial points
+    if (nb > 0) {
+      a = df_add(wlo, df_mul_f(ww, (float)nb / 33.0f));
+      pa = p_lo;
+    }
+    if (nb < 32) {
+      b = df_add(wlo, df_mul_f(ww, (float)(nb + 1) / 33.0f));
+      pb = p_hi;
+    }
+    level = hit ? level + 1 : 0;
   }
   return exp(0.5 * (df_to_double(a) + df_to_double(b)));
 }
