@@ -101,12 +101,14 @@ struct SumDF {
 };
 
 // Split sums.  Every deviation x (J or Q) is split on a power-of-two grid g
-// chosen per item from a bound on |x| (g >= 2^-11 max |x|): x = g m + x_l with
-// m = round(x / g), |m| <= 2^11, and x_l = x - g m (exact).  Window sums of m,
-// m_J^2 and m_J m_Q are exact in int32 (|m m'| <= 2^22, at most 289 terms, on
-// the integer pipe); the remainders' parts, x_l, J^2 - (g_J m_J)^2 =
-// J_l (J + g_J m_J) and J Q - g_J m_J g_Q m_Q = g_J m_J Q_l + J_l Q, are
-// summed in FP32, where their rounding is 2^-11 of that of plain sums.
+// chosen per item from a bound on |x| (g >= 2^-b max |x|): x = g m + x_l with
+// m = round(x / g), |m| <= 2^b, and x_l = x - g m (exact).  Window sums of m,
+// m_J^2 and m_J m_Q are exact in int32 on the integer pipe, and so are
+// n S_mm - S_m^2 and n S_mJ mQ - S_mJ S_mQ: b = split_bits(r) is the largest
+// with n^2 2^(2b) < 2^31 for windows of n = (2r+1)^2 pixels (11 at most).
+// The remainders' parts, x_l, J^2 - (g_J m_J)^2 = J_l (J + g_J m_J) and
+// J Q - g_J m_J g_Q m_Q = g_J m_J Q_l + J_l Q, are summed in FP32, where
+// their rounding is 2^-b of that of plain sums.
 struct SumIG {
   static constexpr int kSub = 1 << 30;
   int h;
@@ -120,12 +122,27 @@ struct IGGrid {
 
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: adding it rounds |v| < 2^22 to an integer
 
+// Bits of the split's integer part for windows of radius r: the largest b
+// <= 11 with ((2r+1)^2)^2 2^(2b) < 2^31 (r = 2: 10, r = 3, 4: 9, r = 8: 7).
+constexpr int split_bits(int rad) {
+  const long long n = (long long)(2 * rad + 1) * (2 * rad + 1);
+  int b = 11;
+  while (b > 0 && n * n * (1LL << (2 * b)) >= (1LL << 31)) --b;
+  return b;
+}
+
+static_assert(split_bits(2) == 10 && split_bits(3) == 9 && split_bits(4) == 9 &&
+                  split_bits(8) == 7 && split_bits(0) == 11,
+              "split bits per window radius");
+
+template <int RAD>
 GFD_D void ig_grid(float bound, float& g, float& ig, float& mg) {
+  constexpr int B = split_bits(RAD);
   int e = 0;
   if (bound > 0.0f && bound < 3e38f) frexpf(bound, &e);  // bound <= 2^e
   if (e < -100) e = -100;
-  g = ldexpf(1.0f, e - 11);
-  ig = ldexpf(1.0f, 11 - e);
+  g = ldexpf(1.0f, e - B);
+  ig = ldexpf(1.0f, B - e);
   mg = kMagic * g;
 }
 
@@ -291,13 +308,15 @@ GFD_D void window_stats(const SumDF& s0, const SumDF& s1, const SumDF& s2, const
 }
 
 // Split sums: the integer parts of n S_JJ - S_J^2 and n S_JQ - S_J S_Q are
-// exact in int64; the remainders' parts are added in FP32.
+// exact in int32 (the split's bits keep every product below 2^31, and E by
+// Cauchy-Schwarz; the differences are formed in modular unsigned arithmetic);
+// the remainders' parts are added in FP32.
 GFD_D void window_stats(const SumIG& s0, const SumIG& s1, const SumIG& s2, const SumIG& s3,
                         float n, float inv_n, const IGGrid& G, float& mJ, float& mQ, float& var,
                         float& cov) {
-  const long long ni = (long long)(int)n;
-  const long long D = ni * s2.h - (long long)s0.h * s0.h;
-  const long long E = ni * s3.h - (long long)s0.h * s1.h;
+  const unsigned ni = (unsigned)(int)n;
+  const int D = (int)(ni * (unsigned)s2.h - (unsigned)s0.h * (unsigned)s0.h);
+  const int E = (int)(ni * (unsigned)s3.h - (unsigned)s0.h * (unsigned)s1.h);
   const float hJ = G.gJ * small_int_to_float(s0.h);  // g_J sum m_J (exact)
   const float hQ = G.gQ * small_int_to_float(s1.h);
   const float lv = fmaf(n, s2.l, -fmaf(2.0f * hJ + s0.l, s0.l, 0.0f));
@@ -305,8 +324,8 @@ GFD_D void window_stats(const SumIG& s0, const SumIG& s1, const SumIG& s2, const
   const float inv2 = inv_n * inv_n;
   mJ = (hJ + s0.l) * inv_n;
   mQ = (hQ + s1.l) * inv_n;
-  var = fmaf(G.gJ * G.gJ, __ll2float_rn(D), lv) * inv2;
-  cov = fmaf(G.gJ * G.gQ, __ll2float_rn(E), lc) * inv2;
+  var = fmaf(G.gJ * G.gJ, __int2float_rn(D), lv) * inv2;
+  cov = fmaf(G.gJ * G.gQ, __int2float_rn(E), lc) * inv2;
 }
 
 // Column-sum update by one input row's deviations (sign +1: the row enters,
@@ -424,8 +443,8 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
     if constexpr (std::is_same<ACC, SumIG>::value) {
       // |J| <= max |u_I| + |c_I| (the bound the inverse row pass recorded)
       const ImgState* S = st + gi;
-      ig_grid(__uint_as_float(__ldcg(&S->absmax[0])) + fabsf(cI), G.gJ, G.igJ, G.mgJ);
-      ig_grid(__uint_as_float(__ldcg(&S->absmax[1])) + fabsf(cP), G.gQ, G.igQ, G.mgQ);
+      ig_grid<RAD>(__uint_as_float(__ldcg(&S->absmax[0])) + fabsf(cI), G.gJ, G.igJ, G.mgJ);
+      ig_grid<RAD>(__uint_as_float(__ldcg(&S->absmax[1])) + fabsf(cP), G.gQ, G.igQ, G.mgQ);
     }
     // input row j of the item is image row y0 - 2r + j, ring slot j % RI
     const int nin = H + 4 * RAD;
