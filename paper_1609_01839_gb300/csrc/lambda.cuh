@@ -173,10 +173,23 @@ GFD_D double warp_sum_dbl(double v) {
 // Sum of vals[i * stride + j] over i < n for each j < m, by the whole block
 // in FP64 (loads bypass L1: the values were written by other blocks).
 // Results land in sums[0..m) (shared), visible to every thread on return.
+// Several columns: one warp per column (a single barrier); one column: the
+// whole block.
 GFD_D void block_sum_columns(const double* vals, int n, int stride, int m, double* red,
                              double* sums) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarp = num_warps();
+  if (m > 1 && (blockDim.x & 31) == 0) {  // whole warps
+    for (int j = warp; j < m; j += nwarp) {
+      double s = 0.0;
+      for (int i = lane; i < n; i += 32) s += __ldcg(&vals[(size_t)i * stride + j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sums[j] = s;
+    }
+    __syncthreads();
+    return;
+  }
   for (int j = 0; j < m; ++j) {
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(&vals[(size_t)i * stride + j]);
