@@ -136,10 +136,11 @@ k_row_r2c(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
     __syncthreads();
     // copy out tile by tile: rows row0 .. row0+rpc-1 of tile t are contiguous
     float2* dst = cplx_plane(d, dst_sel);
-    const int per_tile = rpc * TB / 2;  // 16-byte chunks
+    // 16-byte chunks: rpc * TB / 2 per tile, TB / 2 per row (powers of two)
+    const int lg_pt = __ffs(rpc * TB / 2) - 1, lg_hr = __ffs(TB / 2) - 1;
     for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x) {
-      const int t = c / per_tile, w = c - t * per_tile;
-      const int r = w / (TB / 2), q = w - r * (TB / 2);
+      const int t = c >> lg_pt, w = c & ((1 << lg_pt) - 1);
+      const int r = w >> lg_hr, q = w & ((1 << lg_hr) - 1);
       const float4 v = *reinterpret_cast<const float4*>(outb + r * L + t * TB + 2 * q);
       *reinterpret_cast<float4*>(dst + (size_t)t * M * TB + (size_t)(row0 + r) * TB + 2 * q) = v;
     }
@@ -174,7 +175,8 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
   const int team = threadIdx.x / T, j = threadIdx.x % T;
   const int per_plane = cd.n_img * M / rpc;
   const int n_items = sel1 >= 0 ? 2 * per_plane : per_plane;
-  const int per_tile = rpc * TB / 2;
+  // 16-byte chunks: rpc * TB / 2 per tile, TB / 2 per row (powers of two)
+  const int lg_pt = __ffs(rpc * TB / 2) - 1, lg_hr = __ffs(TB / 2) - 1;
   auto issue = [&](int item) {
     if (item < n_items) {
       int sel = sel0;
@@ -186,8 +188,8 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
       const ImgDesc& d = imgs[cd.img0 + row_c / M];
       const float2* src = cplx_plane(d, sel) + (size_t)(row_c % M) * TB;
       for (int c = threadIdx.x; c < item_elems / 2; c += blockDim.x) {
-        const int t = c / per_tile, w = c - t * per_tile;
-        const int r = w / (TB / 2), q = w - r * (TB / 2);
+        const int t = c >> lg_pt, w = c & ((1 << lg_pt) - 1);
+        const int r = w >> lg_hr, q = w & ((1 << lg_hr) - 1);
         cp_async16(land + r * L + t * TB + 2 * q, src + (size_t)t * M * TB + r * TB + 2 * q);
       }
     }
@@ -256,11 +258,11 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
 // ---------------------------------------------------------------------------
 
 // copy rows 0..M-1 of B columns (row stride TB) into an [M][B] shared tile;
-// a single contiguous block when B == TB.
+// a single contiguous block when B == TB.  B is a power of two.
 GFD_D void issue_tile(float2* dst, const float2* src, int M, int TB, int B) {
-  const int per_row = B / 2;  // 16-byte chunks per row segment
-  for (int c = threadIdx.x; c < M * per_row; c += blockDim.x) {
-    const int a = c / per_row, q = c - a * per_row;
+  const int lg = __ffs(B / 2) - 1;  // 16-byte chunks per row segment: B / 2
+  for (int c = threadIdx.x; c < (M * B) >> 1; c += blockDim.x) {
+    const int a = c >> lg, q = c & ((1 << lg) - 1);
     cp_async16(dst + a * B + 2 * q, src + (size_t)a * TB + 2 * q);
   }
 }
@@ -690,12 +692,20 @@ static int persistent_grid(K kernel, int threads, size_t smem, int n_items, int 
   return (int)(g < n_items ? g : n_items);
 }
 
+// Largest power of two <= v (v >= 1): rows per item and tile widths are
+// powers of two, so the tile copies index by shifts.
+static int floor_pow2(int v) {
+  int p = 1;
+  while (2 * p <= v) p *= 2;
+  return p;
+}
+
 int rows_per_item(int L, int M, int row_threads) {
   const int T = threads_per_team(L);
   int r = (row_threads > 0 ? row_threads : DEF_ROW_THREADS) / T;
   if (r < 1) r = 1;
   if (r > M) r = M;
-  return r;
+  return floor_pow2(r);
 }
 
 // Tile width of a class's spectra = columns per column item: a block of about
@@ -708,7 +718,7 @@ int class_tile_width(int M, int N, int col_threads) {
   int B = threads / T;
   if (B < 2) B = 2;
   if (B > N / 2) B = N / 2;
-  return B;
+  return floor_pow2(B);
 }
 
 static size_t row_r2c_smem(int L, int rpc) {
