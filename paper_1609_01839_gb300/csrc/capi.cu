@@ -1054,8 +1054,10 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   const size_t plane = align256(P * sizeof(float));
   const size_t per_img = (n_real + n_spec) * plane + align256(n_dbl * sizeof(double));
   const size_t descs_bytes = align256(sizeof(AdjDesc) * n);
-  const int n_fft = 11;  // ImgDesc arrays of the DFTs below
-  const size_t fft_bytes = align256(sizeof(ImgDesc) * n) * n_fft;
+  // ImgDesc arrays of the DFTs below: 11 of n entries, then 2 of 2n that
+  // transform two planes of every image in one launch
+  const int n_fft = 13;
+  const size_t fft_bytes = align256(sizeof(ImgDesc) * 2 * n) * n_fft;
   const size_t need = per_img * n + descs_bytes + fft_bytes;
   cudaError_t e;
   if (need > c->adj_ws_bytes) {
@@ -1070,7 +1072,7 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   AdjDesc* d_desc = reinterpret_cast<AdjDesc*>(cur);
   cur += descs_bytes;
   ImgDesc* d_fft = reinterpret_cast<ImgDesc*>(cur);
-  const size_t fft_stride = align256(sizeof(ImgDesc) * n) / sizeof(ImgDesc);
+  const size_t fft_stride = align256(sizeof(ImgDesc) * 2 * n) / sizeof(ImgDesc);
   cur += fft_bytes;
   std::vector<AdjDesc> ad(n);
   std::vector<float*> uEcur(n), hc(n), scratch(n);
@@ -1128,26 +1130,30 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
     a.gy_out = grads[i].g_y;
     a.gh_out = grads[i].g_h;
     // DFT descriptors: r2c(src -> dst) uses u, S, Y; c2r(src -> dst) uses QI, uI
-    auto r2c = [&](int op, const float* src, float2* dst) {
+    auto r2c = [&](int op, const float* src, float2* dst, float2* rows) {
       ImgDesc& q = fd[op][i];
       q = ImgDesc{};
       q.u = const_cast<float*>(src);
-      q.S = reinterpret_cast<float2*>(scratch[i]);
+      q.S = rows;  // the row pass's intermediate
       q.Y = dst;
     };
+    float2* const scr = reinterpret_cast<float2*>(scratch[i]);
     auto c2r = [&](int op, float2* src, float* dst) {
       ImgDesc& q = fd[op][i];
       q = ImgDesc{};
       q.QI = src;
       q.uI = dst;
     };
-    r2c(0, uEcur[i], a.UE);
+    r2c(0, uEcur[i], a.UE, scr);
     c2r(1, a.UI, uIp);  // the recomputed step: U_I, U_p -> u_I, u_p
     c2r(2, a.Up, upp);
-    r2c(3, a.guI, a.GUI);
-    r2c(4, a.gup, a.GUp);
-    r2c(5, hc[i], a.H);
-    r2c(6, imgs[i].y, a.Y);
+    // g_uI, g_up are transformed in one launch (op 12), each through its own
+    // intermediate: the spectra U_I, U_p are free by then (the spectral
+    // adjoint re-forms them from U_E)
+    r2c(3, a.guI, a.GUI, a.UI);
+    r2c(4, a.gup, a.GUp, a.Up);
+    r2c(5, hc[i], a.H, scr);
+    r2c(6, imgs[i].y, a.Y, scr);
     c2r(7, a.gUE, a.gtmp);
     c2r(8, a.gY, a.gtmp);
     c2r(9, a.gH, a.gtmp2);
@@ -1161,14 +1167,19 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
   if ((e = cudaMemcpyAsync(d_desc, ad.data(), sizeof(AdjDesc) * n, cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return map_err(e);
+  // paired transforms: u_I and u_p (inverse), g_uI and g_up (forward)
+  fd[11] = fd[1];
+  fd[11].insert(fd[11].end(), fd[2].begin(), fd[2].end());
+  fd[12] = fd[3];
+  fd[12].insert(fd[12].end(), fd[4].begin(), fd[4].end());
   for (int op = 0; op < n_fft; ++op)
-    if ((e = cudaMemcpyAsync(d_fft + fft_stride * op, fd[op].data(), sizeof(ImgDesc) * n,
+    if ((e = cudaMemcpyAsync(d_fft + fft_stride * op, fd[op].data(), sizeof(ImgDesc) * fd[op].size(),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return map_err(e);
   const Tables t{c->tw, c->d2, c->twdf};
   auto cls = [&](int op) {
     ClassLaunch cl{};
-    cl.cd = ClassDesc{M, N, n, 0, N / 2};
+    cl.cd = ClassDesc{M, N, (int)fd[op].size(), 0, N / 2};
     cl.imgs = d_fft + fft_stride * op;
     cl.st = nullptr;
     return cl;
@@ -1213,16 +1224,14 @@ int gfdeconv_backward_batched(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs
                                  cudaMemcpyDeviceToDevice, s));
     GFD_ADJ_CK(fwd(0));
     GFD_ADJ_CK(launch_adj_recompute(d_desc, n, M, N, k, c->d2, s));
-    GFD_ADJ_CK(adj(1, invP));
-    GFD_ADJ_CK(adj(2, invP));
+    GFD_ADJ_CK(adj(11, invP));  // u_I and u_p
     for (int i0 = 0; i0 < n;) {  // guided-filter adjoint, one launch per run of equal w
       int i1 = i0 + 1;
       while (i1 < n && imgs[i1].w == imgs[i0].w) ++i1;
       GFD_ADJ_CK(launch_adj_guided_filter(d_desc + i0, i1 - i0, M, N, (imgs[i0].w - 1) / 2, s));
       i0 = i1;
     }
-    GFD_ADJ_CK(fwd(3));
-    GFD_ADJ_CK(fwd(4));
+    GFD_ADJ_CK(fwd(12));  // G_UI and G_Up
     GFD_ADJ_CK(launch_adj_spectral(d_desc, n, M, N, c->d2, s));
     GFD_ADJ_CK(adj(7, 1.0f));
     GFD_ADJ_CK(launch_adj_next(d_desc, n, M, N, s));
