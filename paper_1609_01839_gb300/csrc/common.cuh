@@ -24,6 +24,8 @@ GFD_HD int tab_off(int L) { return L - 2; }
 // Number of interpolation nodes for the regularisation-parameter equation
 // (Sec. 3.2, Eq. 11) evaluated per spectral pass.
 constexpr int KNODES = 12;
+constexpr int KNARROW = 8;  // nodes of the first pass from iteration NARROW_FROM on
+constexpr int NARROW_FROM = 5;
 // Fallback passes launched after the fused pass of each iteration (default).
 constexpr int LAMBDA_FALLBACK_PASSES = 4;
 constexpr double LAMBDA_LO = 1e-14;
@@ -120,7 +122,7 @@ struct ImgState {
   int need;          // 1: lambda unresolved, a fallback pass must run
   int status;        // ST_* bits
   int iter;          // iteration index of the pending outputs
-  int pad_;
+  int nk;            // nodes of the pending pass (KNODES, or KNARROW for a narrow first pass)
   double rtol;       // relative width of lambda at which the root search stops
   unsigned int absmax[2];  // bits of max |u_I|, max |u_p| of the current iteration
 };

@@ -311,8 +311,9 @@ __global__ void k_col_plain(ClassDesc cd, const ImgDesc* __restrict__ imgs,
 // in that loop).  A block takes a contiguous range of items and keeps its
 // per-node sums in registers while consecutive items belong to the same
 // image; it publishes them (one partial slot, one counter update) only when
-// the image changes.
-template <int M>
+// the image changes.  NK: the nodes of the pass (KNODES, or KNARROW for the
+// narrow brackets of iterations NARROW_FROM on).
+template <int M, int NK>
 __global__ void __launch_bounds__(M >= 4096 ? 512 : 256, M >= 4096 ? 1 : 2)
 k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
                  const float2* __restrict__ tw, int iter, int row_items) {
@@ -433,7 +434,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
         const float2 r = csub(cmul(Hk, U), Yk);
         const float rr = fmaf(r.x, r.x, r.y * r.y);
         const float a = fmaf(Hk.x, Hk.x, Hk.y * Hk.y);
-        accum_bin(2.0f * rr, a, nodes, acc);  // bins l and N-l
+        accum_bin<NK>(2.0f * rr, a, nodes, acc);  // bins l and N-l
       }
     } else {
       for (int i = 0; i < R; ++i) {
@@ -456,8 +457,8 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
           rA = fmaf(r.x, r.x, r.y * r.y);
         }
         const float2 rb = csub(cmul(HB, UB), YB);
-        accum_bin(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
-        accum_bin(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
+        accum_bin<NK>(rA, fmaf(HA.x, HA.x, HA.y * HA.y), nodes, acc);
+        accum_bin<NK>(fmaf(rb.x, rb.x, rb.y * rb.y), fmaf(HB.x, HB.x, HB.y * HB.y), nodes, acc);
         spec[(size_t)k * B] = U;
       }
     }
@@ -831,15 +832,25 @@ static size_t col_smem(int B, int landings, int works, int nthr) {
          (M <= SMEM_TW_MAX ? (size_t)M * sizeof(float2) : 0);
 }
 
-template <int M>
-static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
+template <int M, int NK>
+static void do_col_fwd_lambda_nk(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
   const int Lc = c.cd.N / 2, B = c.cd.TB;
   const int nthr = B * threads_per_team(M);
   const size_t smem = col_smem<M>(B, 1, 1, nthr);
   const int n_items = c.cd.n_img * (Lc / B);
-  const int grid = persistent_grid(k_col_fwd_lambda<M>, nthr, smem, n_items, c.grid_div);
+  const int grid = persistent_grid(k_col_fwd_lambda<M, NK>, nthr, smem, n_items, c.grid_div);
   const int row_items = c.cd.M / rows_per_item(c.cd.N / 2, c.cd.M, c.row_threads);
-  k_col_fwd_lambda<M><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, iter, row_items);
+  k_col_fwd_lambda<M, NK><<<grid, nthr, smem, s>>>(c.cd, c.imgs, c.st, t.tw, iter, row_items);
+}
+
+// The brackets resolve_warp lays out for iteration `iter` have KNARROW nodes
+// from NARROW_FROM on: the pass evaluates exactly those.
+template <int M>
+static void do_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter, cudaStream_t s) {
+  if (iter >= NARROW_FROM)
+    do_col_fwd_lambda_nk<M, KNARROW>(c, t, iter, s);
+  else
+    do_col_fwd_lambda_nk<M, KNODES>(c, t, iter, s);
 }
 
 cudaError_t launch_col_fwd_lambda(const ClassLaunch& c, const Tables& t, int iter,
@@ -911,7 +922,8 @@ static cudaError_t cfg_col() {
   cudaError_t e;
   if ((e = allow_smem(k_col_plain<M, false>)) != cudaSuccess) return e;
   if ((e = allow_smem(k_col_plain<M, true>)) != cudaSuccess) return e;
-  if ((e = allow_smem(k_col_fwd_lambda<M>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_col_fwd_lambda<M, KNODES>)) != cudaSuccess) return e;
+  if ((e = allow_smem(k_col_fwd_lambda<M, KNARROW>)) != cudaSuccess) return e;
   return allow_smem(k_col_solve_inv<M>);
 }
 

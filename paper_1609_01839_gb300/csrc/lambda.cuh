@@ -24,6 +24,12 @@
 //   of the interpolant.
 // The first pass of each iteration is fused into the forward column FFT and
 // uses a bracket of ratio 4 around an extrapolation of the previous lambdas.
+// From iteration NARROW_FROM on, where the extrapolation comes within a few
+// percent of the root, it evaluates KNARROW = 8 nodes on a bracket of ratio
+// 1.56, whose degree-7 interpolant is as accurate as the degree-11 one on
+// ratio 4 (the strip of analyticity is the same, the bracket's half-width in
+// t three times smaller).  A root outside that bracket lies close to it: the
+// fallback pass takes the ratio-4 bracket next to it.
 #pragma once
 #include "common.cuh"
 #include "df.cuh"
@@ -32,44 +38,59 @@ namespace gfd {
 
 constexpr float INTERP_RATIO = 4.0f;   // largest bracket ratio interpolated
 constexpr float PRIMARY_RATIO = 2.0f;  // primary bracket: [c/2, 2 c]
+constexpr float NARROW_RATIO = 1.25f;  // from iteration NARROW_FROM: [c/1.25, 1.25 c]
+constexpr float NARROW_INTERP_RATIO = 1.6f;  // largest ratio interpolated with KNARROW nodes
 constexpr float INITIAL_LO = 1e-8f, INITIAL_HI = 1e4f;
 constexpr int MODE_GEOM = 0, MODE_CHEB = 1;
 
-// cos(pi j / (KNODES - 1)), j = 0..KNODES-1 (Chebyshev-Lobatto points)
+// cos(pi j / (n - 1)), j = 0..n-1 (Chebyshev-Lobatto points) for n = KNODES
+// and n = KNARROW
 __device__ constexpr float kLobatto[KNODES] = {
     1.0f, 0.9594929736144974f, 0.8412535328311812f, 0.6548607339452851f,
     0.41541501300188644f, 0.14231483827328512f, -0.142314838273285f, -0.4154150130018863f,
     -0.654860733945285f, -0.8412535328311811f, -0.9594929736144974f, -1.0f};
+__device__ constexpr float kLobatto8[KNARROW] = {
+    1.0f, 0.9009688679024191f, 0.6234898018587336f, 0.22252093395631445f,
+    -0.2225209339563144f, -0.6234898018587335f, -0.900968867902419f, -1.0f};
 
-// Node lambda_j (ascending) of a bracket [lo, hi] for the given layout.
-GFD_D float bracket_node(float lo, float hi, int mode, int j) {
+// Node lambda_j (ascending) of a bracket [lo, hi] of nk nodes for the given
+// layout (nodes j >= nk repeat hi and are not evaluated).
+GFD_D float bracket_node(float lo, float hi, int mode, int j, int nk) {
   if (j == 0) return lo;
-  if (j == KNODES - 1) return hi;
-  if (mode == MODE_CHEB)  // Chebyshev-Lobatto in ln(lambda)
-    return lo * exp2f(0.5f * (1.0f - kLobatto[j]) * log2f(hi / lo));
-  return lo * exp2f((float)j / (KNODES - 1) * log2f(hi / lo));
+  if (j >= nk - 1) return hi;
+  if (mode == MODE_CHEB) {  // Chebyshev-Lobatto in ln(lambda)
+    const float c = nk == KNARROW ? kLobatto8[j] : kLobatto[j];
+    return lo * exp2f(0.5f * (1.0f - c) * log2f(hi / lo));
+  }
+  return lo * exp2f((float)j / (nk - 1) * log2f(hi / lo));
 }
 
-GFD_D int bracket_mode(float lo, float hi) { return hi <= INTERP_RATIO * lo ? MODE_CHEB : MODE_GEOM; }
+// Chebyshev nodes (interpolated) for brackets narrow enough for nk nodes,
+// geometric nodes (bracketed) otherwise.
+GFD_D int bracket_mode(float lo, float hi, int nk) {
+  return hi <= (nk == KNARROW ? NARROW_INTERP_RATIO : INTERP_RATIO) * lo ? MODE_CHEB : MODE_GEOM;
+}
 
-// Set the next pass's bracket (single thread).
-GFD_D void set_bracket(ImgState* st, float lo, float hi) {
-  const int mode = bracket_mode(lo, hi);
+// Set the next pass's bracket of nk nodes (single thread).
+GFD_D void set_bracket(ImgState* st, float lo, float hi, int nk = KNODES) {
+  const int mode = bracket_mode(lo, hi, nk);
   st->lo = lo;
   st->hi = hi;
   st->mode = mode;
-  for (int j = 0; j < KNODES; ++j) st->node[j] = bracket_node(lo, hi, mode, j);
+  st->nk = nk;
+  for (int j = 0; j < KNODES; ++j) st->node[j] = bracket_node(lo, hi, mode, j, nk);
 }
 
 // Warp variant: lane j < KNODES writes node j.
-GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane) {
-  const int mode = bracket_mode(lo, hi);
+GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane, int nk = KNODES) {
+  const int mode = bracket_mode(lo, hi, nk);
   if (lane == 0) {
     st->lo = lo;
     st->hi = hi;
     st->mode = mode;
+    st->nk = nk;
   }
-  if (lane < KNODES) st->node[lane] = bracket_node(lo, hi, mode, lane);
+  if (lane < KNODES) st->node[lane] = bracket_node(lo, hi, mode, lane, nk);
   __syncwarp();
 }
 
@@ -80,10 +101,12 @@ GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane) {
 // the same reciprocal error for a given node: a node-dependent bias of ~1e-7
 // in f(lambda_j) that moves the root by ~1e-7 / |d ln f / d ln lambda|,
 // i.e. by percents where f is nearly flat in lambda.
+// NK: the nodes the pass evaluates (acc[NK..KNODES-1] are left alone).
+template <int NK = KNODES>
 GFD_D void accum_bin(float wr, float a, const float* nodes, float* acc) {
   acc[KNODES] += wr;
 #pragma unroll
-  for (int j = 0; j < KNODES; ++j) {
+  for (int j = 0; j < NK; ++j) {
     const float d = a + nodes[j];
     const float q = __fdividef(1.0f, d);
     const float t0 = nodes[j] * q;
@@ -246,19 +269,19 @@ GFD_D df df_div_fast(df a, df b) {  // a / b, error ~2^-44 relative
   return quick_two_sum(q1, r * ib);
 }
 
-GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) {
-  const bool own = lane < KNODES;
+GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane, int nk) {
+  const bool own = lane < nk;
   const df tm = own ? df_from_double(log((double)xm)) : df_make(0.0f);
   // All abscissa differences are scaled by a power of two ~ 1/(node span):
   // exact, and it keeps the products of 11 differences in FP32 range (the
   // sign of S and the root do not depend on the scale).
   const float t0 = __shfl_sync(0xffffffffu, tm.hi, 0);
-  const float tK = __shfl_sync(0xffffffffu, tm.hi, KNODES - 1);
+  const float tK = __shfl_sync(0xffffffffu, tm.hi, nk - 1);
   int ex;
   frexpf(tK - t0, &ex);
   const float sc = ldexpf(1.0f, -ex);
   df prod = df_make(1.0f);
-  for (int n = 0; n < KNODES; ++n) {
+  for (int n = 0; n < nk; ++n) {
     const df tn{__shfl_sync(0xffffffffu, tm.hi, n), __shfl_sync(0xffffffffu, tm.lo, n)};
     if (own && n != lane) {
       const df dd = df_sub(tm, tn);
@@ -274,7 +297,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) 
     s_g[lane] = gm;
   }
   __syncwarp();
-  const float sig = ((KNODES - 1 - j) & 1) ? -1.0f : 1.0f;  // sign of l(t) in the bracket
+  const float sig = ((nk - 1 - j) & 1) ? -1.0f : 1.0f;  // sign of l(t) in the bracket
   df a = s_t[j], b = s_t[j + 1];
   float pa = s_g[j], pb = s_g[j + 1];  // p at the bracket's ends
   int level = 0;                       // windows in a row that held the root
@@ -321,7 +344,7 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane) 
       S.lo += u.lo + q.lo;
     };
 #pragma unroll 2
-    for (int m = 0; m < KNODES; m += 2) {  // registers stay low in the pass kernels
+    for (int m = 0; m < nk; m += 2) {  // nk is even; registers stay low in the pass kernels
       term(m, S0);
       term(m + 1, S1);
     }
@@ -360,6 +383,8 @@ GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int
     st->need = 0;
     if (lam_out) lam_out[iter] = lam;
   }
+  // the first pass of iteration iter + 1 evaluates nk nodes
+  const int nk = iter + 1 >= NARROW_FROM ? KNARROW : KNODES;
   if (isfinite(lam) && lam > 0.0) {
     const float l = (float)lam;
     float lo, hi;
@@ -373,12 +398,19 @@ GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int
       const double prev = st->lam_prev;
       float c = l;
       if (isfinite(prev) && prev > 0.0) c = l * fminf(fmaxf((float)(lam / prev), 0.5f), 2.0f);
-      lo = c / PRIMARY_RATIO;
-      hi = c * PRIMARY_RATIO;
+      const float ratio = nk == KNARROW ? NARROW_RATIO : PRIMARY_RATIO;
+      lo = c / ratio;
+      hi = c * ratio;
     }
     lo = fmaxf(lo, (float)LAMBDA_LO);
-    set_bracket_warp(st, lo, hi, lane);  // ends with __syncwarp()
+    set_bracket_warp(st, lo, hi, lane, nk);  // ends with __syncwarp()
     if (lane == 0) st->lam_prev = lam;
+  } else if (st->nk != nk) {
+    // lambda = inf (or no finite root): the pending bracket is kept, laid
+    // out for the node count of the next first pass
+    const float lo = (float)st->lo, hi = (float)st->hi;
+    __syncwarp();
+    set_bracket_warp(st, lo, hi, lane, nk);
   }
   __syncwarp();
 }
@@ -414,13 +446,15 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
     }
     __syncwarp();
   }
-  // g_m = f(lambda_m) / T - 1, increasing in lambda
-  const float gm = lane < KNODES ? (float)((tot[lane] * invP - T) * st->invT) : 0.0f;
-  const float xm = lane < KNODES ? st->node[lane] : 0.0f;
+  // g_m = f(lambda_m) / T - 1, increasing in lambda, for the nk nodes the
+  // pass evaluated
+  const int nk = st->nk;
+  const float gm = lane < nk ? (float)((tot[lane] * invP - T) * st->invT) : 0.0f;
+  const float xm = lane < nk ? st->node[lane] : 0.0f;
   const float g0 = __shfl_sync(0xffffffffu, gm, 0);
-  const float gK = __shfl_sync(0xffffffffu, gm, KNODES - 1);
+  const float gK = __shfl_sync(0xffffffffu, gm, nk - 1);
   const float lo = __shfl_sync(0xffffffffu, xm, 0);
-  const float hi = __shfl_sync(0xffffffffu, xm, KNODES - 1);
+  const float hi = __shfl_sync(0xffffffffu, xm, nk - 1);
   const int mode = st->mode;
   bool open = true;
   if (!(g0 <= 0.0f)) {  // root below the bracket (or NaN)
@@ -434,16 +468,21 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
       resolve_warp(st, LAMBDA_LO, iter, lam_out, lane);
       return;
     }
-    set_bracket_warp(st, (float)LAMBDA_LO, lo, lane);
+    // below a narrow first bracket: the ratio-4 bracket just under it;
+    // otherwise everything down to the smallest lambda
+    const float nlo = nk == KNARROW ? fmaxf(0.25f * lo, (float)LAMBDA_LO) : (float)LAMBDA_LO;
+    set_bracket_warp(st, nlo, lo, lane);
   } else if (gK < 0.0f) {  // root above the bracket
-    set_bracket_warp(st, hi, fmaxf(st->lam_up, hi * 4.0f), lane);
+    // above a narrow first bracket: the ratio-4 bracket just over it;
+    // otherwise up to the bound from res and |H|^2
+    set_bracket_warp(st, hi, nk == KNARROW ? 4.0f * hi : fmaxf(st->lam_up, hi * 4.0f), lane);
   } else {
     // nodes with g < 0 form a prefix 0..j
-    const unsigned below = __ballot_sync(0xffffffffu, lane < KNODES && gm < 0.0f);
+    const unsigned below = __ballot_sync(0xffffffffu, lane < nk && gm < 0.0f);
     int j = 31 - __clz(below | 1u);
-    if (j > KNODES - 2) j = KNODES - 2;
+    if (j > nk - 2) j = nk - 2;
     if (mode == MODE_CHEB) {
-      const double lam = interp_root_warp(xm, gm, j, st->rtol, lane);
+      const double lam = interp_root_warp(xm, gm, j, st->rtol, lane, nk);
       resolve_warp(st, lam, iter, lam_out, lane);
       open = false;
     } else {

@@ -4,7 +4,8 @@ Eq. 10-11), checked on the CPU in FP64.
 The GPU evaluates f(lambda) = sum_b lambda^2 r_b / (a_b + lambda)^2 at 12
 nodes of a bracket and, for brackets of ratio <= 4, takes the root of the
 degree-11 interpolant in t = ln(lambda) through Chebyshev-Lobatto nodes in t
-as the answer.  These tests restate that layout (not the GPU code) and check
+as the answer (8 nodes, degree 7, on the ratio-1.56 first brackets of later
+iterations).  These tests restate that layout (not the GPU code) and check
 the claim it rests on: in t the poles of f sit at Im t = pi for every
 spectrum, so the interpolated root is within ~1e-10 of the true one on ratio
 4, whereas the same nodes in lambda (poles at lambda = -a_b, close to the
@@ -85,6 +86,18 @@ def test_lambda_space_nodes_do_not(kind):
     # the same 12 nodes placed in lambda fall far short of the 1e-6 tolerance
     # on ratio 4 (poles of f at lambda = -|H_b|^2 next to the bracket)
     assert worst_root_error(kind, 4.0, log_space=False) > 1e-7
+
+
+@pytest.mark.parametrize("kind", ["wide", "zeros", "narrow"])
+def test_eight_nodes_resolve_the_narrow_first_brackets(kind):
+    # from the sixth iteration on the first pass of an iteration takes 8
+    # nodes on [c / 1.25, 1.25 c] (ratio 1.56) about the extrapolated lambda
+    global K
+    saved, K = K, 8
+    try:
+        assert worst_root_error(kind, 1.5625, log_space=True, trials=30) < 1e-9
+    finally:
+        K = saved
 
 
 def test_log_space_error_shrinks_with_the_bracket():
