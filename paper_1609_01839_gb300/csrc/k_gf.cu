@@ -594,7 +594,7 @@ GFD_D void gfw_items(const ClassDesc& cd, const ImgDesc* __restrict__ imgs, ImgS
       for (int k = 0; k < 4; ++k) {
         float inv_n = inv_full;
         if constexpr (TRUNC) inv_n = __frcp_rn(nout * ncol[k]);
-        o[k] = fmaf(SA[k] * inv_n, ic[k], SB[k] * inv_n) + cP;
+        o[k] = fmaf(fmaf(SA[k], ic[k], SB[k]), inv_n, cP);
       }
       if (store) {
         const size_t off = (size_t)((y0 + t) & (M - 1)) * N + gx;
