@@ -269,7 +269,7 @@ int gfdeconv_solve_batched_timed(gfdeconv_ctx* ctx, int n, const gfdeconv_image*
  *   row_threads in {64, 128, 256}: threads per row-pass block (rows per item);
  *   gf_rows in {16, 32, 64}: output rows per guided-filter item;
  * keeping per canvas size the fastest over the phases the shape affects, then
- * times graph replays of the solve with 1, 2 and 4 concurrent chains.  The
+ * times graph replays of the solve with 1 to 4 concurrent chains.  The
  * result applies to the context's later solves and, if `path` is not NULL
  * or "", is merged into that tile-shape file (other canvas sizes kept), which
  * gfdeconv_opts.tune_cache reads at create.  Synchronises `stream`.  Returns

@@ -928,7 +928,7 @@ int gfdeconv_autotune(gfdeconv_ctx* c, int n, const gfdeconv_image* imgs, int it
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = 1e300;
     int pick = cur.chains;
-    for (int q = 1; q <= CHAINS && e == cudaSuccess; q *= 2) {
+    for (int q = 1; q <= CHAINS && e == cudaSuccess; ++q) {
       cur.chains = q;
       c->tune = cur;
       drop_plan(c);
