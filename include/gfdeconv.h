@@ -58,6 +58,10 @@ typedef enum {
                                           root still bracketed: lambda is the
                                           bracket's geometric midpoint, which may
                                           miss the requested lambda_rtol */
+#define GFD_STATUS_COPY_TIMEOUT 32 /* a column pass's bulk copy of a spectrum tile
+                                      did not complete within its wait limit
+                                      (the kernel went on; this image's results
+                                      are not to be trusted) */
 
 /* Arithmetic of the guided filter's window statistics (Sec. 2, Eq. 3-4:
  * mu_k, pbar_k, sigma_k^2 = E[I^2] - mu_k^2 and the covariance are formed from

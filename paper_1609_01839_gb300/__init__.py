@@ -16,7 +16,7 @@ import re
 __all__ = [
     "Context", "GfdError", "lib", "library_path", "header_functions",
     "STATUS_NONCONVERGED", "STATUS_NONFINITE", "STATUS_BAD_PSF", "STATUS_BAD_RHO",
-    "STATUS_PASSES_EXHAUSTED", "VAR_COMPENSATED", "VAR_FP64", "VAR_FP32", "VAR_FP32_RAW",
+    "STATUS_PASSES_EXHAUSTED", "STATUS_COPY_TIMEOUT", "VAR_COMPENSATED", "VAR_FP64", "VAR_FP32", "VAR_FP32_RAW",
     "VAR_DOUBLE_FLOAT",
     "BOUNDARY_PERIODIC", "BOUNDARY_TRUNCATED",
 ]
@@ -31,6 +31,7 @@ STATUS_NONFINITE = 2
 STATUS_BAD_PSF = 4
 STATUS_BAD_RHO = 8
 STATUS_PASSES_EXHAUSTED = 16
+STATUS_COPY_TIMEOUT = 32
 # window-statistics arithmetic of the guided filter (gfdeconv_opts.var_precision)
 VAR_COMPENSATED = 0
 VAR_FP64 = 1

@@ -36,6 +36,7 @@ constexpr int ST_NONFINITE = 2;
 constexpr int ST_BAD_PSF = 4;
 constexpr int ST_BAD_RHO = 8;
 constexpr int ST_PASSES_EXHAUSTED = 16;
+constexpr int ST_COPY_TIMEOUT = 32;
 
 GFD_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 GFD_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -82,6 +83,49 @@ GFD_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memo
 template <int N>
 GFD_D void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One-dimensional bulk copies (the TMA engine) completed on an mbarrier.
+// A block stages a contiguous tile with one instruction from one thread:
+//   mbar_init once; per tile, the issuing thread calls bulk_load (which arms
+//   the barrier with the byte count) and every thread waits with mbar_wait on
+//   the barrier's current phase parity, which then flips.
+// Addresses are 16-byte aligned and sizes multiples of 16 (the tiles are whole
+// column slabs of 256-byte aligned planes).
+GFD_D void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+GFD_D void bulk_load(void* smem_dst, const void* gsrc, unsigned int bytes, unsigned long long* bar) {
+  // earlier generic-proxy reads of the buffer are ordered before the async write
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+GFD_D bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase of the given parity; false if it has not completed after
+// the iteration limit (each try_wait blocks for at most a short, hardware-set
+// time), so that a copy that never lands cannot hang the kernel.
+constexpr int MBAR_WAIT_LIMIT = 1 << 22;
+GFD_D bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  for (int i = 0; i < MBAR_WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a

@@ -257,16 +257,6 @@ k_row_c2r(ClassDesc cd, const ImgDesc* __restrict__ imgs, const float2* __restri
 // tile and team b (threads b, b+B, ...) transforms column c0+b.
 // ---------------------------------------------------------------------------
 
-// copy rows 0..M-1 of B columns (row stride TB) into an [M][B] shared tile;
-// a single contiguous block when B == TB.  B is a power of two.
-GFD_D void issue_tile(float2* dst, const float2* src, int M, int TB, int B) {
-  const int lg = __ffs(B / 2) - 1;  // 16-byte chunks per row segment: B / 2
-  for (int c = threadIdx.x; c < (M * B) >> 1; c += blockDim.x) {
-    const int a = c >> lg, q = c & ((1 << lg) - 1);
-    cp_async16(dst + a * B + 2 * q, src + (size_t)a * TB + 2 * q);
-  }
-}
-
 // Setup / utility column FFT (not pipelined): plane src -> dst, in place
 // allowed; B columns (inside one tile) per block.  Loads and stores walk the
 // B columns fastest (coalesced rows of the tile); the in-place stages walk a
@@ -323,6 +313,7 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   __shared__ double s_tot[KNODES + 1];
   __shared__ int s_flag;
   __shared__ WarpAcc s_wacc;
+  __shared__ __align__(8) unsigned long long s_bar;  // completion of the landing tile
   const int B = cd.TB;
   const int Lc = cd.N / 2;
   const int cpi = Lc / B;
@@ -346,16 +337,20 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
   const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
+  // the item's S tile is one contiguous slab: one bulk copy by thread 0,
+  // completed on s_bar; H and Y of the item are read after its transform,
+  // so they are only prefetched into L2
+  if (threadIdx.x == 0) mbar_init(&s_bar);
+  __syncthreads();
+  unsigned int parity = 0;
   auto issue = [&](int item) {
     if (item < stop) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
-      issue_tile(landS, d.S + off, M, B, B);
-      // H and Y of the item are read after its transform: start them now
+      if (threadIdx.x == 0) bulk_load(landS, d.S + off, (unsigned int)(tile * sizeof(float2)), &s_bar);
       prefetch_l2(d.H + off, (unsigned int)(tile * sizeof(float2)));
       prefetch_l2(d.Y + off, (unsigned int)(tile * sizeof(float2)));
     }
-    cp_async_commit();
   };
   float acc[KNODES + 1];
 #pragma unroll
@@ -392,10 +387,11 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   warp_acc_clear(&s_wacc);  // first use follows the loop's __syncthreads()
   issue(first);
   for (int item = first; item < stop; ++item) {
-    cp_async_wait<0>();
-    __syncthreads();
     const int gi = cd.img0 + item / cpi;
     const int t = item % cpi;
+    if (!mbar_wait(&s_bar, parity)) atomicOr(&st[gi].status, ST_COPY_TIMEOUT);
+    parity ^= 1;
+    __syncthreads();
     if (gi != cur) {
       if (count > 0) flush();
       cur = gi;
@@ -466,7 +462,6 @@ k_col_fwd_lambda(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
     ++count;
   }
   if (count > 0) flush();
-  cp_async_wait<0>();
 }
 
 // Fallback evaluation of Eq. 11 over the stored spectrum U_E for images whose
@@ -578,30 +573,36 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
   float2* landU = smem;
   float2* workI = landU + tile;
   float2* workP = workI + B * ts;
+  __shared__ __align__(8) unsigned long long s_bar;  // completion of the landing tile
   const float2* twM = tw + tab_off(M);
   if constexpr (M <= SMEM_TW_MAX) {
     float2* stw = workP + B * ts;
     for (int i = threadIdx.x; i < M; i += blockDim.x) stw[i] = twM[i];
     twM = stw;  // visible after the loop's first __syncthreads()
   }
+  if (threadIdx.x == 0) mbar_init(&s_bar);
+  __syncthreads();
+  unsigned int parity = 0;
   // b-fastest mapping for tile I/O, team-fastest for the in-place stages
   const int b = threadIdx.x % B, j = threadIdx.x / B;
   const int bf = T >= 16 ? threadIdx.x / T : b, jf = T >= 16 ? threadIdx.x % T : j;
+  // the item's U_E tile: one bulk copy by thread 0, completed on s_bar; H and
+  // Y of the item are prefetched into L2
   auto issue = [&](int item) {
     if (item < n_items) {
       const ImgDesc& d = imgs[cd.img0 + item / cpi];
       const size_t off = (size_t)(item % cpi) * tile;
-      issue_tile(landU, d.S + off, M, B, B);
+      if (threadIdx.x == 0) bulk_load(landU, d.S + off, (unsigned int)(tile * sizeof(float2)), &s_bar);
       prefetch_l2(d.H + off, (unsigned int)(tile * sizeof(float2)));
       prefetch_l2(d.Y + off, (unsigned int)(tile * sizeof(float2)));
     }
-    cp_async_commit();
   };
   issue(blockIdx.x);
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    cp_async_wait<0>();
-    __syncthreads();
     const int gi = cd.img0 + item / cpi;
+    if (!mbar_wait(&s_bar, parity)) atomicOr(&st[gi].status, ST_COPY_TIMEOUT);
+    parity ^= 1;
+    __syncthreads();
     const ImgDesc& d = imgs[gi];
     const int t = item % cpi;
     const int col = t * B + b;
@@ -654,7 +655,6 @@ k_col_solve_inv(ClassDesc cd, const ImgDesc* __restrict__ imgs, ImgState* st,
       qp[k * B] = bufP[phys(p)];
     }
   }
-  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
