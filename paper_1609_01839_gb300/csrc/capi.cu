@@ -138,6 +138,7 @@ struct gfdeconv_ctx {
   cudaStream_t side[CHAINS - 1] = {};  // further chains of a captured solve
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[CHAINS - 1] = {};
+  cudaEvent_t ev_in[CHAINS - 1] = {};  // a chain's host inputs have landed
   char* ws = nullptr;
   size_t ws_bytes = 0;
   ImgDesc* d_imgs = nullptr;
@@ -485,12 +486,18 @@ cudaError_t record(gfdeconv_ctx* c, Plan& pl, cudaStream_t s, Timer* tm = nullpt
   if (chains && !tm && pl.nparts > 1 && !pl.parts[1].empty()) {
     GFD_CK(cudaEventRecord(c->ev_fork, s));
     for (int q = 1; q < pl.nparts; ++q) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_fork, 0));
+    // host inputs chain after chain: each chain's copies start once the
+    // previous chain's have landed, so the first chain computes after its own
+    // share of the transfer instead of after the interleaved whole
     GFD_CK(issue_imgs(pl.parts[0], true, s));
+    if (hc) GFD_CK(cudaEventRecord(c->ev_in[0], s));
     GFD_CK(setup(pl.parts[0], s));
     GFD_CK(iterate(pl.parts[0], s));
     GFD_CK(issue_imgs(pl.parts[0], false, s));
     for (int q = 1; q < pl.nparts; ++q) {
+      if (hc) GFD_CK(cudaStreamWaitEvent(c->side[q - 1], c->ev_in[q - 1], 0));
       GFD_CK(issue_imgs(pl.parts[q], true, c->side[q - 1]));
+      if (hc && q < pl.nparts - 1) GFD_CK(cudaEventRecord(c->ev_in[q], c->side[q - 1]));
       GFD_CK(setup(pl.parts[q], c->side[q - 1]));
       GFD_CK(iterate(pl.parts[q], c->side[q - 1]));
       GFD_CK(issue_imgs(pl.parts[q], false, c->side[q - 1]));
@@ -777,7 +784,8 @@ int gfdeconv_create(gfdeconv_ctx** out, int cuda_device, const gfdeconv_opts* op
   }
   for (int q = 0; q < CHAINS - 1; ++q) {
     if ((e = cudaStreamCreateWithFlags(&c->side[q], cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&c->ev_join[q], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->ev_in[q], cudaEventDisableTiming)) != cudaSuccess) {
       gfdeconv_destroy(c);
       return map_err(e);
     }
@@ -811,6 +819,7 @@ void gfdeconv_destroy(gfdeconv_ctx* c) {
   for (int q = 0; q < CHAINS - 1; ++q) {
     if (c->side[q]) cudaStreamDestroy(c->side[q]);
     if (c->ev_join[q]) cudaEventDestroy(c->ev_join[q]);
+    if (c->ev_in[q]) cudaEventDestroy(c->ev_in[q]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
