@@ -96,3 +96,22 @@ def test_binding_struct_matches_header_layout(libpath):
     fields = re.findall(r"[\w\*\s]+?\b(\w+)\s*[,;]", body)
     assert names == fields, (names, fields)
     assert ctypes.sizeof(gfd.Image) == 8 + 4 + 4 + 8 + 4 + 4 + 8 + 8 + 8 + 9 * 8
+
+
+def test_binding_constants_match_the_header(libpath):
+    """Every status bit, arithmetic, boundary and error code the header
+    defines has the same value in the binding."""
+    import paper_1609_01839_gb300 as gfd
+    text = open(os.path.join(ROOT, "include", "gfdeconv.h")).read()
+    defs = dict(re.findall(r"#define GFD_((?:STATUS|VAR|BOUNDARY)_\w+)\s+(-?\d+)", text))
+    defs.update(re.findall(r"GFD_(ERR_\w+)\s*=\s*(-?\d+)", text))
+    assert {"STATUS_PASSES_EXHAUSTED", "STATUS_COPY_TIMEOUT", "VAR_COMPENSATED",
+            "BOUNDARY_TRUNCATED", "ERR_INVALID_ARG"} <= set(defs)
+    for name, value in defs.items():
+        if hasattr(gfd, name):
+            assert getattr(gfd, name) == int(value), name
+    for name in ("STATUS_NONCONVERGED", "STATUS_NONFINITE", "STATUS_BAD_PSF", "STATUS_BAD_RHO",
+                 "STATUS_PASSES_EXHAUSTED", "STATUS_COPY_TIMEOUT", "VAR_COMPENSATED", "VAR_FP64",
+                 "VAR_FP32", "VAR_FP32_RAW", "VAR_DOUBLE_FLOAT", "BOUNDARY_PERIODIC",
+                 "BOUNDARY_TRUNCATED", "ERR_INVALID_ARG", "ERR_SCRATCH_LIMIT"):
+        assert getattr(gfd, name) == int(defs[name]), name
