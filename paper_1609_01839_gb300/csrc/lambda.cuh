@@ -43,6 +43,14 @@ constexpr float NARROW_INTERP_RATIO = 1.6f;  // largest ratio interpolated with 
 constexpr float INITIAL_LO = 1e-8f, INITIAL_HI = 1e4f;
 constexpr int MODE_GEOM = 0, MODE_CHEB = 1;
 
+// Lanes of the warp that runs a per-image update (threads 0..31 of the
+// block): the whole warp, or every thread of a block smaller than a warp
+// (the column passes of 8- and 16-row canvases run 16 threads per block).
+GFD_D int upd_lanes() { return blockDim.x >= 32 ? 32 : (int)blockDim.x; }
+GFD_D unsigned int upd_mask() {
+  return blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+}
+
 // cos(pi j / (n - 1)), j = 0..n-1 (Chebyshev-Lobatto points) for n = KNODES
 // and n = KNARROW
 __device__ constexpr float kLobatto[KNODES] = {
@@ -91,7 +99,7 @@ GFD_D void set_bracket_warp(ImgState* st, float lo, float hi, int lane, int nk =
     st->nk = nk;
   }
   if (lane < KNODES) st->node[lane] = bracket_node(lo, hi, mode, lane, nk);
-  __syncwarp();
+  __syncwarp(upd_mask());
 }
 
 // One bin's contribution: wr = (Hermitian weight) * r, a = |H|^2.
@@ -275,14 +283,14 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane, 
   // All abscissa differences are scaled by a power of two ~ 1/(node span):
   // exact, and it keeps the products of 11 differences in FP32 range (the
   // sign of S and the root do not depend on the scale).
-  const float t0 = __shfl_sync(0xffffffffu, tm.hi, 0);
-  const float tK = __shfl_sync(0xffffffffu, tm.hi, nk - 1);
+  const float t0 = __shfl_sync(upd_mask(), tm.hi, 0);
+  const float tK = __shfl_sync(upd_mask(), tm.hi, nk - 1);
   int ex;
   frexpf(tK - t0, &ex);
   const float sc = ldexpf(1.0f, -ex);
   df prod = df_make(1.0f);
   for (int n = 0; n < nk; ++n) {
-    const df tn{__shfl_sync(0xffffffffu, tm.hi, n), __shfl_sync(0xffffffffu, tm.lo, n)};
+    const df tn{__shfl_sync(upd_mask(), tm.hi, n), __shfl_sync(upd_mask(), tm.lo, n)};
     if (own && n != lane) {
       const df dd = df_sub(tm, tn);
       prod = df_mul(prod, df{dd.hi * sc, dd.lo * sc});
@@ -296,12 +304,14 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane, 
     s_c[lane] = c;
     s_g[lane] = gm;
   }
-  __syncwarp();
+  __syncwarp(upd_mask());
   const float sig = ((nk - 1 - j) & 1) ? -1.0f : 1.0f;  // sign of l(t) in the bracket
   df a = s_t[j], b = s_t[j + 1];
   float pa = s_g[j], pb = s_g[j + 1];  // p at the bracket's ends
   int level = 0;                       // windows in a row that held the root
-  const float frac32 = (float)(lane + 1) / 33.0f;
+  const int nl = upd_lanes();  // trial points per round
+  const float inv_np1 = 1.0f / (float)(nl + 1);
+  const float frac32 = (float)(lane + 1) * inv_np1;
   for (int round = 0; round < 24; ++round) {
     const df width = df_sub(b, a);
     if (df_to_double(width) <= rtol) break;  // absolute in t: relative in lambda
@@ -351,18 +361,18 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane, 
     const df Sv = df_add(quick_two_sum(S0.hi, S0.lo), quick_two_sum(S1.hi, S1.lo));
     const bool neg = at_node ? (node_g < 0.0f) : (sig * Sv.hi < 0.0f);
     const float pv = at_node ? node_g : ell * (Sv.hi + Sv.lo);  // p(t), for the estimate
-    const unsigned below = __ballot_sync(0xffffffffu, neg);
+    const unsigned below = __ballot_sync(upd_mask(), neg);
     // the interpolant increases: trial points below the root form a prefix
     const int nb = __popc(below);  // lanes 0..nb-1 are below the root
-    const float p_lo = __shfl_sync(0xffffffffu, pv, nb > 0 ? nb - 1 : 0);
-    const float p_hi = __shfl_sync(0xffffffffu, pv, nb < 32 ? nb : 31);
-    const bool hit = nb > 0 && nb < 32;  // the root lies between two trial points
+    const float p_lo = __shfl_sync(upd_mask(), pv, nb > 0 ? nb - 1 : 0);
+    const float p_hi = __shfl_sync(upd_mask(), pv, nb < nl ? nb : nl - 1);
+    const bool hit = nb > 0 && nb < nl;  // the root lies between two trial points
     if (nb > 0) {
-      a = df_add(wlo, df_mul_f(ww, (float)nb / 33.0f));
+      a = df_add(wlo, df_mul_f(ww, (float)nb * inv_np1));
       pa = p_lo;
     }
-    if (nb < 32) {
-      b = df_add(wlo, df_mul_f(ww, (float)(nb + 1) / 33.0f));
+    if (nb < nl) {
+      b = df_add(wlo, df_mul_f(ww, (float)(nb + 1) * inv_np1));
       pb = p_hi;
     }
     level = hit ? level + 1 : 0;
@@ -372,11 +382,12 @@ GFD_D double interp_root_warp(float xm, float gm, int j, double rtol, int lane, 
 
 // Record lambda_k and set the bracket of iteration k+1's fused first pass.
 // lambda jumps by a factor of 2..150 from the first iteration (u_E = 0) to
-// the second and by 1/8..8 to the third; later it changes smoothly, so the
-// bracket is centred on the extrapolation lambda_k (lambda_k / lambda_{k-1})
-// (ratio clamped to [1/2, 2]).  The first two use geometric nodes, resolved by
-// one more pass; the later ones are narrow enough (ratio 4) for the
-// interpolation to resolve them in the fused pass itself.
+// the second, and mostly falls to 0.2..1.2 of it in the third; later it
+// changes smoothly, so the bracket is centred on the extrapolation
+// lambda_k (lambda_k / lambda_{k-1}) (ratio clamped to [1/2, 2]).  The second
+// iteration's bracket has geometric nodes, resolved by one more pass; the
+// third's, [0.28, 1.1] lambda_1, and the later ones are narrow enough
+// (ratio <= 4) for the interpolation to resolve them in the fused pass itself.
 GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int lane) {
   if (lane == 0) {
     st->lam = lam;
@@ -392,8 +403,8 @@ GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int
       lo = l;
       hi = 150.0f * l;
     } else if (iter == 1) {
-      lo = 0.125f * l;
-      hi = 8.0f * l;
+      lo = 0.28f * l;
+      hi = 1.1f * l;
     } else {
       const double prev = st->lam_prev;
       float c = l;
@@ -409,10 +420,10 @@ GFD_D void resolve_warp(ImgState* st, double lam, int iter, double* lam_out, int
     // lambda = inf (or no finite root): the pending bracket is kept, laid
     // out for the node count of the next first pass
     const float lo = (float)st->lo, hi = (float)st->hi;
-    __syncwarp();
+    __syncwarp(upd_mask());
     set_bracket_warp(st, lo, hi, lane, nk);
   }
-  __syncwarp();
+  __syncwarp(upd_mask());
 }
 
 // Consume the totals of the pass that just completed for this image (tot:
@@ -444,18 +455,20 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
       const float t = sqrtf((float)T / (float)resinf);
       st->lam_up = fminf(1e30f, (float)st->amax * t / (1.0f - t));
     }
-    __syncwarp();
+    __syncwarp(upd_mask());
   }
   // g_m = f(lambda_m) / T - 1, increasing in lambda, for the nk nodes the
   // pass evaluated
   const int nk = st->nk;
   const float gm = lane < nk ? (float)((tot[lane] * invP - T) * st->invT) : 0.0f;
   const float xm = lane < nk ? st->node[lane] : 0.0f;
-  const float g0 = __shfl_sync(0xffffffffu, gm, 0);
-  const float gK = __shfl_sync(0xffffffffu, gm, nk - 1);
-  const float lo = __shfl_sync(0xffffffffu, xm, 0);
-  const float hi = __shfl_sync(0xffffffffu, xm, nk - 1);
+  const float g0 = __shfl_sync(upd_mask(), gm, 0);
+  const float gK = __shfl_sync(upd_mask(), gm, nk - 1);
+  const float lo = __shfl_sync(upd_mask(), xm, 0);
+  const float hi = __shfl_sync(upd_mask(), xm, nk - 1);
   const int mode = st->mode;
+  // a missed first bracket whose root is expected close to it
+  const bool near = nk == KNARROW || (primary && iter == 2 && mode == MODE_CHEB);
   bool open = true;
   if (!(g0 <= 0.0f)) {  // root below the bracket (or NaN)
     if (!isfinite(g0)) {
@@ -468,17 +481,18 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
       resolve_warp(st, LAMBDA_LO, iter, lam_out, lane);
       return;
     }
-    // below a narrow first bracket: the ratio-4 bracket just under it;
-    // otherwise everything down to the smallest lambda
-    const float nlo = nk == KNARROW ? fmaxf(0.25f * lo, (float)LAMBDA_LO) : (float)LAMBDA_LO;
+    // below a narrow first bracket, or the third iteration's first bracket
+    // (four passes to go): the ratio-4 bracket just under it; otherwise
+    // everything down to the smallest lambda
+    const float nlo = near ? fmaxf(0.25f * lo, (float)LAMBDA_LO) : (float)LAMBDA_LO;
     set_bracket_warp(st, nlo, lo, lane);
   } else if (gK < 0.0f) {  // root above the bracket
     // above a narrow first bracket: the ratio-4 bracket just over it;
     // otherwise up to the bound from res and |H|^2
-    set_bracket_warp(st, hi, nk == KNARROW ? 4.0f * hi : fmaxf(st->lam_up, hi * 4.0f), lane);
+    set_bracket_warp(st, hi, near ? 4.0f * hi : fmaxf(st->lam_up, hi * 4.0f), lane);
   } else {
     // nodes with g < 0 form a prefix 0..j
-    const unsigned below = __ballot_sync(0xffffffffu, lane < nk && gm < 0.0f);
+    const unsigned below = __ballot_sync(upd_mask(), lane < nk && gm < 0.0f);
     int j = 31 - __clz(below | 1u);
     if (j > nk - 2) j = nk - 2;
     if (mode == MODE_CHEB) {
@@ -486,7 +500,7 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
       resolve_warp(st, lam, iter, lam_out, lane);
       open = false;
     } else {
-      const float nlo = __shfl_sync(0xffffffffu, xm, j), nhi = __shfl_sync(0xffffffffu, xm, j + 1);
+      const float nlo = __shfl_sync(upd_mask(), xm, j), nhi = __shfl_sync(upd_mask(), xm, j + 1);
       set_bracket_warp(st, nlo, nhi, lane);
     }
   }
@@ -495,7 +509,7 @@ GFD_D void lambda_update_warp(ImgState* st, const double* tot, double P, bool pr
     if (last_chance) {  // the pass schedule ran out with the bracket still open
       if (lane == 0) st->status |= ST_PASSES_EXHAUSTED;
       const double mid = sqrt((double)st->lo * (double)st->hi);
-      __syncwarp();
+      __syncwarp(upd_mask());
       resolve_warp(st, mid, iter, lam_out, lane);
     }
   }
