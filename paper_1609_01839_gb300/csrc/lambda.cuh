@@ -258,12 +258,13 @@ GFD_D bool last_item(unsigned int* counter, unsigned int n_items, int* s_flag) {
 // logarithms are formed in FP64 and carried as double-float, as are the
 // barycentric weights w_m = 1 / prod_{n != m} (t_m - t_n) of the actual nodes.
 // Inside (t_j, t_{j+1}) the interpolant is p(t) = l(t) S(t) with
-// l(t) = prod_m (t - t_m), whose sign there is (-1)^(KNODES-1-j), and
+// l(t) = prod_m (t - t_m), whose sign there is (-1)^(nk-1-j) (nk nodes), and
 // S(t) = sum_m w_m g_m / (t - t_m) (the first barycentric form), so the sign
 // of p at a point needs S alone, one double-float quotient per node.  The
 // root is bracketed by multisection: every lane evaluates the sign at its own
 // trial point and the bracket shrinks to the two trial points that straddle
-// the root.  After a plain round (32 points across the bracket) the next
+// the root.  After a plain round (one point per lane, spread evenly across
+// the bracket; 32 lanes, or the block's threads if fewer) the next
 // round's points sit in a window about the secant estimate from p at the
 // bracket's ends (window half-width 1/16, then 1/256, then 1/4096 of the
 // bracket while the root keeps falling inside it; a round whose window misses
